@@ -1,0 +1,181 @@
+/*
+ * pic.h -- C-ABI of libpic.so, the GB300 (sm_103a) hot path of the explicit electrostatic
+ * 1D3V PIC/MCC simulation of a capacitively coupled RF argon discharge
+ * (Vass, Palla & Hartmann, arXiv 2109.04469, §2 "Computational method", steps 1-6).
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (PIC_OK) on success, a negative PIC_ERR_* code on failure, or a positive
+ *    PIC_WARN_* code.  No exception or abort crosses the ABI.  pic_strerror() names a code.
+ *  - A handle works on one CUDA stream (given at pic_init) and is not thread-safe.
+ *  - Device memory: the caller allocates ONE device workspace of pic_workspace_bytes()
+ *    bytes (256-byte aligned) and keeps it alive until pic_free(); the library allocates no
+ *    device memory.  Host memory of the handle itself is owned by the library.
+ *  - Arrays passed to pic_get_* / pic_set_* / pic_diag are HOST arrays owned by the caller.
+ *  - Units are SI unless a name says otherwise (_ev: electronvolt).
+ *  - Species index: 0 = electrons, 1 = Ar+ ions.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_ERR_PARAM (-1)      /* invalid parameter or argument */
+#define PIC_ERR_CUDA (-2)       /* a CUDA call failed; the handle should be freed */
+#define PIC_ERR_CAPACITY (-3)   /* births exceeded capacity_per_species; excess dropped */
+#define PIC_ERR_NONFINITE (-4)  /* a velocity became NaN or infinite */
+#define PIC_ERR_WORKSPACE (-5)  /* workspace missing, too small or misaligned */
+#define PIC_WARN_UNSTABLE 1     /* omega_pe*dt > 2: the leapfrog stability bound of §3.5 */
+
+#define PIC_FP64 0 /* FP64 particle state; bit-for-bit the oracle's step contract */
+#define PIC_FP32 1 /* FP32 cell + offset particle state, FP64 field solve and diagnostics */
+
+#define PIC_N_COUNTERS 16
+/* counter slots of pic_diag_out.counters / pic_get_accum():
+ * 0,1 electrons absorbed at x=0 / x=L; 2,3 ions absorbed at x=0 / x=L; 4 electron
+ * reflections; 5 ion-induced electrons emitted; 6,7,8 electron elastic / excitation /
+ * ionization events; 9,10 ion isotropic / charge-transfer events; 11,12 electron / ion
+ * null-collision candidates; 13 EEPF samples; 14 sum of sampled energies in 2^-20 eV;
+ * 15 births dropped for lack of capacity. */
+
+/* The problem statement of §2 and Table 1 (gap, pressure, gas temperature, RF amplitude
+ * and frequency, N_t, grid, weight W, R, gamma, nominal 1 cm^2 area of §3) plus the
+ * synthetic initial load and diagnostic layout. */
+typedef struct pic_params {
+  double gap_m;           /* L, electrode gap (§2 step 1) */
+  double pressure_pa;     /* p, argon pressure (Table 1); 0 = no gas */
+  double gas_temp_k;      /* T_g (Table 1) */
+  double v_rf_amp_v;      /* phi_0 of V(t) = phi_0 cos(2 pi f t) at x = 0 (§2) */
+  double f_rf_hz;         /* f (§2) */
+  int32_t steps_per_rf;   /* N_t, dt = 1/(f N_t) (§2) */
+  int32_t n_cells;        /* N_x - 1 >= 2, dx = L/n_cells (§2 step 1) */
+  double weight;          /* W, real particles per superparticle (§3.4), > 0 */
+  double refl_e;          /* R, electron reflection probability in [0,1] (§2 step 5) */
+  double gamma_see;       /* gamma, ion-induced emission yield in [0,1] (§2 step 5) */
+  double area_m2;         /* nominal electrode area (§3: 1 cm^2) */
+  double init_te_ev;      /* initial electron temperature of the uniform load */
+  double see_energy_ev;   /* energy of ion-induced electrons (reading C-11) */
+  int64_t init_per_species;     /* superparticles of each species in the initial load */
+  int64_t capacity_per_species; /* array capacity, >= init_per_species, < 2^31 */
+  uint64_t seed;          /* Philox key: (lo32(seed), hi32(seed) xor instance) */
+  uint32_t instance;      /* simulation index within an ensemble */
+  int32_t precision;      /* PIC_FP64 or PIC_FP32 */
+  int32_t eepf_bins;      /* EEPF histogram bins over [0, eepf_emax_ev) */
+  double eepf_emax_ev;
+  int32_t fedf_bins;      /* wall flux-energy histogram bins over [0, fedf_emax_ev) */
+  double fedf_emax_ev;
+} pic_params;
+
+typedef struct pic_handle pic_handle;
+
+/* Output of pic_diag().  The caller sets the three sizes and the array pointers (host
+ * memory it owns, or NULL to skip an array); the library fills everything else. */
+typedef struct pic_diag_out {
+  int32_t n_x;        /* must equal n_cells + 1 when n_e / n_i are given */
+  int32_t eepf_bins;  /* must equal the handle's eepf_bins when eepf arrays are given */
+  int32_t fedf_bins;  /* must equal the handle's fedf_bins when fedf arrays are given */
+  double *n_e, *n_i;                 /* [n_x] time-averaged densities, m^-3 (§3.1) */
+  double *eepf_energy, *eepf;        /* [eepf_bins] bin centres (eV) and EEPF, with
+                                        sum sqrt(e) f de = 1 (§3.1) */
+  double *fedf_energy, *fedf_e, *fedf_i; /* [fedf_bins] wall flux-energy distributions,
+                                            sum f de = 1 (§3.4) */
+  uint64_t counters[PIC_N_COUNTERS];
+  int64_t steps_averaged, count_e, count_i;
+  double ion_flux_left, ion_flux_right, ion_flux; /* m^-2 s^-1 (§3.4 Fig. 11; C-21) */
+  double n_e_center, te_center_ev;                /* at L/2 (reading C-19) */
+  double omega_pe_dt, omega_pe_dt_max;            /* §3.5 (centre / peak density) */
+  double p_coll_e, p_coll_i;                      /* 1 - exp(-nu_max dt) (§3.5) */
+  double cfl_max;                                 /* max |vx| dt/dx over electrons (§1, §3.5) */
+  double lambda_d, dx_over_lambda_d, n_debye;     /* §3.5 (readings C-19, C-20) */
+  int32_t status;                                 /* sticky device status (PIC_OK or error) */
+} pic_diag_out;
+
+/* Device workspace size for p (validates p).  Returns PIC_ERR_PARAM on invalid p. */
+int pic_workspace_bytes(const pic_params* p, size_t* bytes);
+
+/* Create a simulation in the caller's workspace on cuda_stream (a cudaStream_t, or NULL
+ * for the legacy default stream): derives the constants of §2, builds the collision tables
+ * (reading C-XS) and drive table on the host, loads the initial uniform Maxwellian
+ * population (reading C-22) and deposits it.  Synchronises the stream before returning. */
+int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void* cuda_stream,
+             pic_handle** out);
+
+/* Enqueue n_steps timesteps (§2 steps 1-6, in that order) on the handle's stream without
+ * synchronising.  Returns the sticky status observed at the end of an earlier call. */
+int pic_step(pic_handle* h, int64_t n_steps);
+
+/* Wait for the stream and return the sticky device status. */
+int pic_sync(pic_handle* h);
+
+/* Timing variant of pic_step for benchmarks: runs n_steps steps with CUDA events recorded on
+ * the handle's stream around each of the step's two launches, waits for each step, and ADDS
+ * the measured device milliseconds to ms_out[0] (particle pass: §2 steps 3-6 and the deposit
+ * of step 1) and ms_out[1] (compaction, with the field solve of §2 steps 1-2 for the next
+ * step running beside it in the same launch).  Same results as pic_step. */
+int pic_step_profiled(pic_handle* h, int64_t n_steps, double* ms_out);
+
+/* Synchronise and reduce the accumulators into physical diagnostics (host side). */
+int pic_diag(pic_handle* h, pic_diag_out* out);
+
+/* Copy one species' particles to host arrays of length >= capacity; *n_out = count.
+ * FP32 handles convert to FP64 at this boundary. */
+int pic_get_particles(pic_handle* h, int species, double* x, double* vx, double* vy,
+                      double* vz, uint32_t* id, int64_t capacity, int64_t* n_out);
+
+/* Replace one species' particles from host arrays of length n and set its id counter,
+ * then redeposit its charge (§2 step 1).  Synchronises. */
+int pic_set_particles(pic_handle* h, int species, const double* x, const double* vx,
+                      const double* vy, const double* vz, const uint32_t* id, int64_t n,
+                      uint32_t next_id);
+
+/* Number of particles of each species (synchronises). */
+int pic_counts(pic_handle* h, int64_t* n_e, int64_t* n_i);
+
+/* Copy the current charge counts (int64, 2^32 per superparticle, [n_cells+1] each) and the
+ * potential / field of the current step (solved from those counts at the end of the
+ * previous step, at init, or by pic_solve_field) to host arrays (any may be NULL).
+ * Synchronises. */
+int pic_get_grid(pic_handle* h, int64_t* charge_e, int64_t* charge_i, double* phi,
+                 double* efield);
+
+/* Solve the field (§2 step 2) of the current charge at V(t_n) of the current step index,
+ * without advancing time or touching the accumulators.  Enqueued on the stream. */
+int pic_solve_field(pic_handle* h);
+
+/* Raw accumulators for bit-exact comparison: acc_e / acc_i [n_x] (sums of the counts per
+ * averaged step), eepf [eepf_bins], fedf_e / fedf_i [fedf_bins], counters [16];
+ * *steps = averaged steps.  Any pointer may be NULL.  Synchronises. */
+int pic_get_accum(pic_handle* h, double* acc_e, double* acc_i, uint64_t* eepf,
+                  uint64_t* fedf_e, uint64_t* fedf_i, uint64_t* counters, int64_t* steps);
+
+/* Zero the accumulators (start of a measurement window after convergence, §2). */
+int pic_reset_averages(pic_handle* h);
+
+/* Set the step index n (selects V(t_n) and the random streams).  Enqueued. */
+int pic_set_step(pic_handle* h, uint32_t step);
+
+/* Current step index and id counters (synchronises). */
+int pic_get_step(pic_handle* h, uint32_t* step, uint32_t* next_id_e, uint32_t* next_id_i);
+
+/* Replace a species' cumulative collision-fraction table ([100001][4] doubles, contract of
+ * the cross-section lookup) and nu_max; for statistical tests with synthetic rates. */
+int pic_override_table(pic_handle* h, int species, const double* table, double nu_max);
+
+/* Derived constants (dt, dx, n_g, nu_max e/i, P_max e/i) into out[7]. */
+int pic_get_derived(pic_handle* h, double* out);
+
+/* Release the handle (host memory only; the caller frees the workspace afterwards). */
+void pic_free(pic_handle* h);
+
+/* Static string for a return code. */
+const char* pic_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -296,7 +296,7 @@ static void build_tables(orc_sim *S) {
 static void lookup(const double *F, double eps, double out[3]) {
   double t = eps * XS_INV_DE;
   double kf = floor(t);
-  if (kf >= (double)(XS_NODES - 1)) {
+  if (!(kf < (double)(XS_NODES - 1))) { /* also catches a non-finite energy */
     const double *a = F + 4 * (XS_NODES - 1);
     out[0] = a[0]; out[1] = a[1]; out[2] = a[2];
     return;

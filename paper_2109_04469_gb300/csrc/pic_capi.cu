@@ -1,0 +1,669 @@
+// pic_capi.cu -- the C-ABI of libpic (include/pic.h): parameter checks, the derived
+// constants and host tables of the step contract, workspace layout, launches, diagnostics.
+//
+// Host arithmetic that feeds the FP64 kernels (constants, pivots, drive and collision
+// tables) is compiled with -ffp-contract=off and follows the contract's operation order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pic.h"
+#include "pic_dev.cuh"
+#include "pic_launch.h"
+
+namespace {
+
+using namespace pic;
+
+// CODATA 2018
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kKb = 1.380649e-23;
+constexpr double kTwo32 = 4294967296.0;
+
+// Closed-form cross sections of the project (reading C-XS; Phelps' data of §2 step 6 is not
+// available).  eps in eV, sigma in m^2.
+double sigma_e(int proc, double eps) {
+  if (proc == 0) {
+    const double x = eps / 10.0;
+    return 1e-20 * (6.0 * std::exp(-eps / 0.07) + 25.0 * (x * x) / std::pow(1.0 + x * x, 1.3));
+  }
+  if (proc == 1) {
+    if (eps <= kEExc) return 0.0;
+    return 1.6e-20 * std::log(eps / kEExc) / (eps / kEExc);
+  }
+  if (eps <= kEIon) return 0.0;  // Lotz (1967), a = 4.5e-14 cm^2 eV^2, q = 6
+  return 2.7e-17 * std::log(eps / kEIon) / (eps * kEIon);
+}
+
+// sigma * g of Ar+ - Ar against the centre-of-mass energy eps (eV)
+double sigma_g_i(int proc, double eps, double spd2_rel) {
+  if (proc == 0) return 1e-19 * std::sqrt((0.5 + eps) * spd2_rel) / std::sqrt(1.0 + eps / 100.0);
+  if (eps <= 0.0) return 0.0;
+  const double a = 7.0 - 0.55 * std::log(eps);
+  return 1e-20 * (a * a) * std::sqrt(eps * spd2_rel);
+}
+
+struct Derived {
+  double dx, inv_dx, inv_2dx, dt, ng, qm_dt[2], emfac_e, spd2_e, mu, emfac_rel, spd2_rel,
+      emfac_ilab, mr2, sig_e, sig_i, v_see, efac, rfac, mi;
+  double numax[2], pmax[2];
+};
+
+Derived derive(const pic_params& p) {
+  Derived d;
+  d.dx = p.gap_m / (double)p.n_cells;
+  d.inv_dx = 1.0 / d.dx;
+  d.inv_2dx = 0.5 * d.inv_dx;
+  d.dt = 1.0 / (p.f_rf_hz * (double)p.steps_per_rf);
+  d.ng = p.pressure_pa / (kKb * p.gas_temp_k);
+  d.mi = 39.948 * kAmu;
+  d.qm_dt[0] = (-kQe / kMe) * d.dt;
+  d.qm_dt[1] = (kQe / d.mi) * d.dt;
+  d.emfac_e = (0.5 * kMe) / kQe;
+  d.spd2_e = (2.0 * kQe) / kMe;
+  d.mu = 0.5 * d.mi;
+  d.emfac_rel = (0.5 * d.mu) / kQe;
+  d.spd2_rel = (2.0 * kQe) / d.mu;
+  d.emfac_ilab = (0.5 * d.mi) / kQe;
+  d.mr2 = (2.0 * kMe) / d.mi;
+  d.sig_e = std::sqrt((p.init_te_ev * kQe) / kMe);
+  d.sig_i = std::sqrt((kKb * p.gas_temp_k) / d.mi);
+  d.v_see = std::sqrt(p.see_energy_ev * d.spd2_e);
+  d.efac = (kQe * p.weight) / ((p.area_m2 * kEps0) * kTwo32);
+  d.rfac = d.efac * d.dx;
+  return d;
+}
+
+// nu_m at the table nodes, nu_max (reading C-8), cumulative fractions [k][4] (contract 2.4)
+void build_tables(const pic_params& p, Derived& d, std::vector<double>& Fe,
+                  std::vector<double>& Fi) {
+  std::vector<double> nu((size_t)kXsNodes * 3);
+  for (int s = 0; s < 2; ++s) {
+    double numax = 0.0;
+    for (int k = 0; k < kXsNodes; ++k) {
+      const double eps = (double)k / kXsInvDe;
+      double* n = &nu[(size_t)3 * k];
+      if (s == 0) {
+        const double v = std::sqrt(eps * d.spd2_e);
+        for (int m = 0; m < 3; ++m) n[m] = d.ng * sigma_e(m, eps) * v;
+      } else {
+        n[0] = d.ng * sigma_g_i(0, eps, d.spd2_rel);
+        n[1] = d.ng * sigma_g_i(1, eps, d.spd2_rel);
+        n[2] = 0.0;
+      }
+      const double tot = (n[0] + n[1]) + n[2];
+      if (tot > numax) numax = tot;
+    }
+    d.numax[s] = numax;
+    d.pmax[s] = 1.0 - std::exp(-numax * d.dt);  // §3.5
+    std::vector<double>& F = (s == 0) ? Fe : Fi;
+    F.assign((size_t)kXsNodes * 4, 0.0);
+    for (int k = 0; k < kXsNodes; ++k) {
+      const double* n = &nu[(size_t)3 * k];
+      const double c1 = n[0];
+      const double c2 = c1 + n[1];
+      const double c3 = c2 + n[2];
+      F[(size_t)4 * k + 0] = numax > 0.0 ? c1 / numax : 0.0;
+      F[(size_t)4 * k + 1] = numax > 0.0 ? c2 / numax : 0.0;
+      F[(size_t)4 * k + 2] = numax > 0.0 ? c3 / numax : 0.0;
+    }
+  }
+}
+
+bool valid(const pic_params* p) {
+  if (!p) return false;
+  const bool fin = std::isfinite(p->gap_m) && std::isfinite(p->pressure_pa) &&
+                   std::isfinite(p->gas_temp_k) && std::isfinite(p->v_rf_amp_v) &&
+                   std::isfinite(p->f_rf_hz) && std::isfinite(p->weight) &&
+                   std::isfinite(p->refl_e) && std::isfinite(p->gamma_see) &&
+                   std::isfinite(p->area_m2) && std::isfinite(p->init_te_ev) &&
+                   std::isfinite(p->see_energy_ev) && std::isfinite(p->eepf_emax_ev) &&
+                   std::isfinite(p->fedf_emax_ev);
+  return fin && p->gap_m > 0 && p->pressure_pa >= 0 && p->gas_temp_k > 0 && p->f_rf_hz > 0 &&
+         p->steps_per_rf >= 1 && p->n_cells >= 2 && p->n_cells <= 4096 && p->weight > 0 &&
+         p->refl_e >= 0 && p->refl_e <= 1 && p->gamma_see >= 0 && p->gamma_see <= 1 &&
+         p->area_m2 > 0 && p->init_te_ev >= 0 && p->see_energy_ev >= 0 &&
+         p->init_per_species >= 0 && p->capacity_per_species >= p->init_per_species &&
+         p->capacity_per_species >= 1 && p->capacity_per_species < (int64_t(1) << 31) - kChunk &&
+         (p->precision == PIC_FP64) && p->eepf_bins >= 1 && p->eepf_bins <= (1 << 20) &&
+         p->eepf_emax_ev > 0 && p->fedf_bins >= 1 && p->fedf_bins <= (1 << 20) &&
+         p->fedf_emax_ev > 0;
+}
+
+// Bump allocator over the workspace (first pass with base 0 measures the size).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* r = reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T);
+    return r;
+  }
+};
+
+void carve(const pic_params& p, char* base, DevCtx& K, size_t* total) {
+  Carver c{base};
+  const int nx = p.n_cells + 1;
+  const int nch = (int)((p.capacity_per_species + kChunk - 1) / kChunk);
+  const size_t cap = (size_t)nch * kChunk;
+  K.nchunk_max = nch;
+  K.st = c.take<DevState>(1);
+  for (int s = 0; s < 2; ++s) {
+    K.x[s] = c.take<double>(cap);
+    K.vx[s] = c.take<double>(cap);
+    K.vy[s] = c.take<double>(cap);
+    K.vz[s] = c.take<double>(cap);
+    K.id[s] = c.take<unsigned>(cap);
+  }
+  K.C = c.take<unsigned long long>((size_t)4 * nx);
+  K.phi = c.take<double>(nx);
+  K.E = c.take<double>(nx);
+  K.acc = c.take<double>((size_t)2 * nx);
+  K.inv_den = c.take<double>(nx);
+  K.vtab = c.take<double>((size_t)p.steps_per_rf);
+  K.F[0] = c.take<double>((size_t)kXsNodes * 4);
+  K.F[1] = c.take<double>((size_t)kXsNodes * 4);
+  K.eepf = c.take<unsigned long long>((size_t)p.eepf_bins);
+  K.fedf = c.take<unsigned long long>((size_t)2 * p.fedf_bins);
+  K.counters = c.take<unsigned long long>(kNumCounters);
+  for (int s = 0; s < 2; ++s) {
+    K.hole_idx[s] = c.take<int>(cap);
+    K.hole_cnt[s] = c.take<int>(nch);
+    K.eb_cnt[s] = c.take<int>(nch);
+    K.eb[s] = c.take<double>(4 * cap);
+    K.hole_sorted[s] = c.take<int>(cap);
+  }
+  K.ib_cnt = c.take<int>(nch);
+  K.ib = c.take<double>(4 * cap);
+  *total = (c.off + 255) & ~size_t(255);
+}
+
+// The null-collision test u < P_max with u = (2k+1) 2^-53 (k a 52-bit integer) holds exactly
+// when 2k+1 < C, C = ceil(P_max 2^53) (an integer, exact in double), i.e. k < floor(C/2).
+unsigned long long null_threshold(double pmax) {
+  const double c = std::ceil(std::ldexp(pmax, 53));
+  return (unsigned long long)c / 2ull;
+}
+
+int status_code(int st) {
+  if (st & kStNonfinite) return PIC_ERR_NONFINITE;
+  if (st & kStCapacity) return PIC_ERR_CAPACITY;
+  return PIC_OK;
+}
+
+}  // namespace
+
+struct pic_handle {
+  pic_params p;
+  Derived d;
+  DevCtx K;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  int push_grid;
+  int last_status;
+};
+
+#define PIC_CUDA(call)                        \
+  do {                                        \
+    if ((call) != cudaSuccess) {              \
+      (void)cudaGetLastError();               \
+      return PIC_ERR_CUDA;                    \
+    }                                         \
+  } while (0)
+
+extern "C" {
+
+int pic_workspace_bytes(const pic_params* p, size_t* bytes) {
+  if (!valid(p) || !bytes) return PIC_ERR_PARAM;
+  DevCtx K;
+  carve(*p, nullptr, K, bytes);
+  return PIC_OK;
+}
+
+int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void* cuda_stream,
+             pic_handle** out) {
+  if (!valid(p) || !out) return PIC_ERR_PARAM;
+  *out = nullptr;
+  size_t need = 0;
+  DevCtx K;
+  std::memset(&K, 0, sizeof K);
+  carve(*p, nullptr, K, &need);
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return PIC_ERR_WORKSPACE;
+  pic_handle* h = new (std::nothrow) pic_handle;
+  if (!h) return PIC_ERR_PARAM;
+  h->p = *p;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->ws = static_cast<char*>(workspace);
+  h->ws_bytes = workspace_bytes;
+  h->last_status = PIC_OK;
+  carve(*p, h->ws, K, &need);
+  Derived& d = h->d;
+  d = derive(*p);
+  std::vector<double> Fe, Fi;
+  build_tables(*p, d, Fe, Fi);
+  const int nc = p->n_cells, nx = nc + 1;
+  std::vector<double> inv_den((size_t)nx, 0.0);
+  double den = 2.0;
+  for (int j = 1; j <= nc - 1; ++j) {
+    inv_den[j] = 1.0 / den;
+    den = 2.0 - inv_den[j];
+  }
+  std::vector<double> vtab((size_t)p->steps_per_rf);
+  for (int k = 0; k < p->steps_per_rf; ++k)
+    vtab[k] = p->v_rf_amp_v * std::cos((6.283185307179586 * (double)k) / (double)p->steps_per_rf);
+
+  K.nc = nc;
+  K.nx = nx;
+  K.steps_per_rf = p->steps_per_rf;
+  K.eepf_bins = p->eepf_bins;
+  K.fedf_bins = p->fedf_bins;
+  K.cap = p->capacity_per_species;
+  K.L = p->gap_m;
+  K.dx = d.dx;
+  K.inv_dx = d.inv_dx;
+  K.inv_2dx = d.inv_2dx;
+  K.dt = d.dt;
+  K.efac = d.efac;
+  K.rfac = d.rfac;
+  K.half_L = 0.5 * p->gap_m;
+  K.half_dx = 0.5 * d.dx;
+  K.qm_dt[0] = d.qm_dt[0];
+  K.qm_dt[1] = d.qm_dt[1];
+  K.emfac_e = d.emfac_e;
+  K.spd2_e = d.spd2_e;
+  K.emfac_rel = d.emfac_rel;
+  K.spd2_rel = d.spd2_rel;
+  K.emfac_ilab = d.emfac_ilab;
+  K.mr2 = d.mr2;
+  K.sig_i = d.sig_i;
+  K.v_see = d.v_see;
+  K.sig_load[0] = d.sig_e;
+  K.sig_load[1] = d.sig_i;
+  K.pmax[0] = d.pmax[0];
+  K.pmax[1] = d.pmax[1];
+  K.null_kthr[0] = null_threshold(d.pmax[0]);
+  K.null_kthr[1] = null_threshold(d.pmax[1]);
+  // the EEPF window |x - L/2| < dx/2 lies in cells (nc-1)/2 .. nc/2, one cell of margin
+  K.eepf_jlo = std::max(0, (nc - 1) / 2 - 1);
+  K.eepf_jhi = std::min(nc - 1, nc / 2 + 1);
+  K.refl = p->refl_e;
+  K.gamma = p->gamma_see;
+  K.eepf_inv_de = (double)p->eepf_bins / p->eepf_emax_ev;
+  K.fedf_inv_de = (double)p->fedf_bins / p->fedf_emax_ev;
+  K.key0 = (unsigned)p->seed;
+  K.key1 = (unsigned)(p->seed >> 32) ^ p->instance;
+  h->K = K;
+
+  int dev = 0, sms = 0;
+  cudaStream_t st = h->stream;
+  auto fail = [&](int code) {
+    (void)cudaGetLastError();
+    delete h;
+    return code;
+  };
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      configure_kernels(nx) != cudaSuccess)
+    return fail(PIC_ERR_CUDA);
+  const int bps = push_fp64_blocks_per_sm(nx);
+  h->push_grid = std::max(1, std::min(2 * K.nchunk_max, sms * bps));
+
+  DevState s0;
+  std::memset(&s0, 0, sizeof s0);
+  s0.n[0] = s0.n[1] = p->init_per_species;
+  s0.n_snap[0] = s0.n_snap[1] = p->init_per_species;
+  s0.next_id[0] = s0.next_id[1] = (unsigned)p->init_per_species;
+  if (cudaMemsetAsync(h->ws, 0, need, st) != cudaSuccess ||
+      cudaMemcpyAsync(K.st, &s0, sizeof s0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync((void*)K.inv_den, inv_den.data(), sizeof(double) * nx,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync((void*)K.vtab, vtab.data(), sizeof(double) * vtab.size(),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync((void*)K.F[0], Fe.data(), sizeof(double) * Fe.size(),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync((void*)K.F[1], Fi.data(), sizeof(double) * Fi.size(),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return fail(PIC_ERR_CUDA);
+  for (int s = 0; s < 2; ++s) {
+    if (launch_init_load(K, s, p->init_per_species, st) != cudaSuccess ||
+        launch_deposit(K, s, 0, p->init_per_species, st) != cudaSuccess)
+      return fail(PIC_ERR_CUDA);
+  }
+  if (launch_field(K, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(PIC_ERR_CUDA);
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_step(pic_handle* h, int64_t n_steps) {
+  if (!h || n_steps < 0) return PIC_ERR_PARAM;
+  for (int64_t i = 0; i < n_steps; ++i) {
+    if (launch_push_fp64(h->K, h->push_grid, h->stream) != cudaSuccess ||
+        launch_compact_field(h->K, h->stream) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return PIC_ERR_CUDA;
+    }
+  }
+  return h->last_status;
+}
+
+int pic_step_profiled(pic_handle* h, int64_t n_steps, double* ms_out) {
+  if (!h || n_steps < 0 || !ms_out) return PIC_ERR_PARAM;
+  cudaEvent_t ev[3];
+  for (int k = 0; k < 3; ++k)
+    if (cudaEventCreate(&ev[k]) != cudaSuccess) {
+      for (int m = 0; m < k; ++m) cudaEventDestroy(ev[m]);
+      (void)cudaGetLastError();
+      return PIC_ERR_CUDA;
+    }
+  int rc = PIC_OK;
+  for (int64_t i = 0; i < n_steps && rc == PIC_OK; ++i) {
+    float t[2];
+    if (cudaEventRecord(ev[0], h->stream) != cudaSuccess ||
+        launch_push_fp64(h->K, h->push_grid, h->stream) != cudaSuccess ||
+        cudaEventRecord(ev[1], h->stream) != cudaSuccess ||
+        launch_compact_field(h->K, h->stream) != cudaSuccess ||
+        cudaEventRecord(ev[2], h->stream) != cudaSuccess ||
+        cudaEventSynchronize(ev[2]) != cudaSuccess ||
+        cudaEventElapsedTime(&t[0], ev[0], ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t[1], ev[1], ev[2]) != cudaSuccess) {
+      rc = PIC_ERR_CUDA;
+      break;
+    }
+    ms_out[0] += (double)t[0];
+    ms_out[1] += (double)t[1];
+  }
+  for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+  if (rc != PIC_OK) {
+    (void)cudaGetLastError();
+    return rc;
+  }
+  return h->last_status;
+}
+
+int pic_sync(pic_handle* h) {
+  if (!h) return PIC_ERR_PARAM;
+  int st = 0;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy(&st, &h->K.st->status, sizeof st, cudaMemcpyDeviceToHost));
+  h->last_status = status_code(st);
+  return h->last_status;
+}
+
+int pic_counts(pic_handle* h, int64_t* n_e, int64_t* n_i) {
+  if (!h) return PIC_ERR_PARAM;
+  DevState s;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy(&s, h->K.st, sizeof s, cudaMemcpyDeviceToHost));
+  if (n_e) *n_e = s.n[0];
+  if (n_i) *n_i = s.n[1];
+  return PIC_OK;
+}
+
+int pic_get_step(pic_handle* h, uint32_t* step, uint32_t* next_id_e, uint32_t* next_id_i) {
+  if (!h) return PIC_ERR_PARAM;
+  DevState s;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy(&s, h->K.st, sizeof s, cudaMemcpyDeviceToHost));
+  if (step) *step = s.step;
+  if (next_id_e) *next_id_e = s.next_id[0];
+  if (next_id_i) *next_id_i = s.next_id[1];
+  return PIC_OK;
+}
+
+int pic_get_particles(pic_handle* h, int species, double* x, double* vx, double* vy,
+                      double* vz, uint32_t* id, int64_t capacity, int64_t* n_out) {
+  if (!h || species < 0 || species > 1 || capacity < 0) return PIC_ERR_PARAM;
+  DevState s;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy(&s, h->K.st, sizeof s, cudaMemcpyDeviceToHost));
+  const int64_t n = s.n[species];
+  if (n_out) *n_out = n;
+  const int64_t m = std::min(n, capacity);
+  if (m > 0) {
+    const DevCtx& K = h->K;
+    cudaStream_t st = h->stream;
+    if (x) PIC_CUDA(cudaMemcpyAsync(x, K.x[species], m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (vx) PIC_CUDA(cudaMemcpyAsync(vx, K.vx[species], m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (vy) PIC_CUDA(cudaMemcpyAsync(vy, K.vy[species], m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (vz) PIC_CUDA(cudaMemcpyAsync(vz, K.vz[species], m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (id) PIC_CUDA(cudaMemcpyAsync(id, K.id[species], m * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    PIC_CUDA(cudaStreamSynchronize(st));
+  }
+  return n > capacity ? PIC_ERR_PARAM : PIC_OK;
+}
+
+int pic_set_particles(pic_handle* h, int species, const double* x, const double* vx,
+                      const double* vy, const double* vz, const uint32_t* id, int64_t n,
+                      uint32_t next_id) {
+  if (!h || species < 0 || species > 1 || n < 0 || n > h->p.capacity_per_species)
+    return PIC_ERR_PARAM;
+  if (n > 0 && (!x || !vx || !vy || !vz || !id)) return PIC_ERR_PARAM;
+  const DevCtx& K = h->K;
+  cudaStream_t st = h->stream;
+  DevState s;
+  PIC_CUDA(cudaStreamSynchronize(st));
+  PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
+  if (n > 0) {
+    PIC_CUDA(cudaMemcpyAsync(K.x[species], x, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    PIC_CUDA(cudaMemcpyAsync(K.vx[species], vx, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    PIC_CUDA(cudaMemcpyAsync(K.vy[species], vy, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    PIC_CUDA(cudaMemcpyAsync(K.vz[species], vz, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    PIC_CUDA(cudaMemcpyAsync(K.id[species], id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  }
+  s.n[species] = n;
+  s.n_snap[species] = n;
+  s.next_id[species] = next_id;
+  PIC_CUDA(cudaMemcpyAsync(K.st, &s, sizeof s, cudaMemcpyHostToDevice, st));
+  const int buf = s.step & 1;
+  PIC_CUDA(cudaMemsetAsync(K.C + (size_t)(buf * 2 + species) * K.nx, 0,
+                           sizeof(unsigned long long) * K.nx, st));
+  PIC_CUDA(launch_deposit(K, species, buf, n, st));
+  PIC_CUDA(launch_field(K, st));
+  PIC_CUDA(cudaStreamSynchronize(st));
+  return PIC_OK;
+}
+
+int pic_get_grid(pic_handle* h, int64_t* charge_e, int64_t* charge_i, double* phi,
+                 double* efield) {
+  if (!h) return PIC_ERR_PARAM;
+  const DevCtx& K = h->K;
+  DevState s;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
+  const int buf = s.step & 1;
+  const size_t nb = sizeof(int64_t) * K.nx;
+  if (charge_e) PIC_CUDA(cudaMemcpy(charge_e, K.C + (size_t)(buf * 2) * K.nx, nb, cudaMemcpyDeviceToHost));
+  if (charge_i) PIC_CUDA(cudaMemcpy(charge_i, K.C + (size_t)(buf * 2 + 1) * K.nx, nb, cudaMemcpyDeviceToHost));
+  if (phi) PIC_CUDA(cudaMemcpy(phi, K.phi, sizeof(double) * K.nx, cudaMemcpyDeviceToHost));
+  if (efield) PIC_CUDA(cudaMemcpy(efield, K.E, sizeof(double) * K.nx, cudaMemcpyDeviceToHost));
+  return PIC_OK;
+}
+
+int pic_solve_field(pic_handle* h) {
+  if (!h) return PIC_ERR_PARAM;
+  PIC_CUDA(launch_field(h->K, h->stream));
+  return PIC_OK;
+}
+
+int pic_get_accum(pic_handle* h, double* acc_e, double* acc_i, uint64_t* eepf,
+                  uint64_t* fedf_e, uint64_t* fedf_i, uint64_t* counters, int64_t* steps) {
+  if (!h) return PIC_ERR_PARAM;
+  const DevCtx& K = h->K;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  if (acc_e) PIC_CUDA(cudaMemcpy(acc_e, K.acc, sizeof(double) * K.nx, cudaMemcpyDeviceToHost));
+  if (acc_i) PIC_CUDA(cudaMemcpy(acc_i, K.acc + K.nx, sizeof(double) * K.nx, cudaMemcpyDeviceToHost));
+  if (eepf) PIC_CUDA(cudaMemcpy(eepf, K.eepf, sizeof(uint64_t) * K.eepf_bins, cudaMemcpyDeviceToHost));
+  if (fedf_e) PIC_CUDA(cudaMemcpy(fedf_e, K.fedf, sizeof(uint64_t) * K.fedf_bins, cudaMemcpyDeviceToHost));
+  if (fedf_i) PIC_CUDA(cudaMemcpy(fedf_i, K.fedf + K.fedf_bins, sizeof(uint64_t) * K.fedf_bins, cudaMemcpyDeviceToHost));
+  if (counters) PIC_CUDA(cudaMemcpy(counters, K.counters, sizeof(uint64_t) * kNumCounters, cudaMemcpyDeviceToHost));
+  if (steps) {
+    DevState s;
+    PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
+    *steps = s.steps_avg;
+  }
+  return PIC_OK;
+}
+
+int pic_reset_averages(pic_handle* h) {
+  if (!h) return PIC_ERR_PARAM;
+  const DevCtx& K = h->K;
+  cudaStream_t st = h->stream;
+  PIC_CUDA(cudaMemsetAsync(K.acc, 0, sizeof(double) * 2 * K.nx, st));
+  PIC_CUDA(cudaMemsetAsync(K.eepf, 0, sizeof(uint64_t) * K.eepf_bins, st));
+  PIC_CUDA(cudaMemsetAsync(K.fedf, 0, sizeof(uint64_t) * 2 * K.fedf_bins, st));
+  PIC_CUDA(cudaMemsetAsync(K.counters, 0, sizeof(uint64_t) * kNumCounters, st));
+  PIC_CUDA(cudaMemsetAsync(&K.st->steps_avg, 0, sizeof(long long), st));
+  return PIC_OK;
+}
+
+int pic_set_step(pic_handle* h, uint32_t step) {
+  if (!h) return PIC_ERR_PARAM;
+  PIC_CUDA(launch_set_step(h->K, step, h->stream));
+  PIC_CUDA(launch_field(h->K, h->stream));  // the field of the new step's drive value
+  return PIC_OK;
+}
+
+int pic_override_table(pic_handle* h, int species, const double* table, double nu_max) {
+  if (!h || species < 0 || species > 1 || !table || !(nu_max >= 0) || !std::isfinite(nu_max))
+    return PIC_ERR_PARAM;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy((void*)h->K.F[species], table, sizeof(double) * kXsNodes * 4,
+                      cudaMemcpyHostToDevice));
+  h->d.numax[species] = nu_max;
+  h->d.pmax[species] = 1.0 - std::exp(-nu_max * h->d.dt);
+  h->K.pmax[species] = h->d.pmax[species];
+  h->K.null_kthr[species] = null_threshold(h->d.pmax[species]);
+  return PIC_OK;
+}
+
+int pic_get_derived(pic_handle* h, double* out) {
+  if (!h || !out) return PIC_ERR_PARAM;
+  const double v[7] = {h->d.dt, h->d.dx, h->d.ng, h->d.numax[0], h->d.numax[1],
+                       h->d.pmax[0], h->d.pmax[1]};
+  std::memcpy(out, v, sizeof v);
+  return PIC_OK;
+}
+
+int pic_diag(pic_handle* h, pic_diag_out* out) {
+  if (!h || !out) return PIC_ERR_PARAM;
+  const pic_params& p = h->p;
+  const DevCtx& K = h->K;
+  const int nc = p.n_cells, nx = nc + 1;
+  if ((out->n_e || out->n_i) && out->n_x != nx) return PIC_ERR_PARAM;
+  if ((out->eepf || out->eepf_energy) && out->eepf_bins != p.eepf_bins) return PIC_ERR_PARAM;
+  if ((out->fedf_e || out->fedf_i || out->fedf_energy) && out->fedf_bins != p.fedf_bins)
+    return PIC_ERR_PARAM;
+  const int rc = pic_sync(h);
+  if (rc == PIC_ERR_CUDA) return rc;
+  std::vector<double> acc((size_t)2 * nx);
+  std::vector<uint64_t> eepf(p.eepf_bins), fedf((size_t)2 * p.fedf_bins);
+  DevState s;
+  PIC_CUDA(cudaMemcpy(acc.data(), K.acc, sizeof(double) * 2 * nx, cudaMemcpyDeviceToHost));
+  PIC_CUDA(cudaMemcpy(eepf.data(), K.eepf, sizeof(uint64_t) * eepf.size(), cudaMemcpyDeviceToHost));
+  PIC_CUDA(cudaMemcpy(fedf.data(), K.fedf, sizeof(uint64_t) * fedf.size(), cudaMemcpyDeviceToHost));
+  PIC_CUDA(cudaMemcpy(out->counters, K.counters, sizeof(uint64_t) * kNumCounters, cudaMemcpyDeviceToHost));
+  PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
+  // max |vx| over the electrons for the CFL number
+  PIC_CUDA(cudaMemsetAsync(&K.st->vmax_bits, 0, sizeof(unsigned long long), h->stream));
+  PIC_CUDA(launch_max_abs(K.vx[0], s.n[0], &K.st->vmax_bits, h->stream));
+  unsigned long long vbits = 0;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy(&vbits, &K.st->vmax_bits, sizeof vbits, cudaMemcpyDeviceToHost));
+  double vmax;
+  std::memcpy(&vmax, &vbits, sizeof vmax);
+
+  const Derived& d = h->d;
+  const int64_t steps = s.steps_avg;
+  out->steps_averaged = steps;
+  out->count_e = s.n[0];
+  out->count_i = s.n[1];
+  out->status = rc;
+  const double W = p.weight, A = p.area_m2;
+  const double dens_fac = W / ((A * d.dx) * kTwo32);
+  std::vector<double> ne((size_t)nx);
+  for (int j = 0; j < nx; ++j) {
+    const double vol = (j == 0 || j == nc) ? 0.5 : 1.0;  // reading C-5
+    const double st = steps > 0 ? (double)steps : 1.0;
+    ne[j] = (acc[j] / st) * dens_fac / vol;
+    if (out->n_e) out->n_e[j] = ne[j];
+    if (out->n_i) out->n_i[j] = (acc[nx + j] / st) * dens_fac / vol;
+  }
+  // EEPF with sum sqrt(e) f de = 1 (§3.1)
+  const double de = p.eepf_emax_ev / p.eepf_bins;
+  double tot = 0.0;
+  for (uint64_t v : eepf) tot += (double)v;
+  for (int b = 0; b < p.eepf_bins; ++b) {
+    const double ec = (b + 0.5) * de;
+    if (out->eepf_energy) out->eepf_energy[b] = ec;
+    if (out->eepf) out->eepf[b] = tot > 0 ? (double)eepf[b] / (std::sqrt(ec) * de * tot) : 0.0;
+  }
+  // flux-energy distributions with sum f de = 1 (§3.4)
+  const double fde = p.fedf_emax_ev / p.fedf_bins;
+  double tf[2] = {0.0, 0.0};
+  for (int sp = 0; sp < 2; ++sp)
+    for (int b = 0; b < p.fedf_bins; ++b) tf[sp] += (double)fedf[(size_t)sp * p.fedf_bins + b];
+  for (int b = 0; b < p.fedf_bins; ++b) {
+    if (out->fedf_energy) out->fedf_energy[b] = (b + 0.5) * fde;
+    if (out->fedf_e) out->fedf_e[b] = tf[0] > 0 ? (double)fedf[b] / (fde * tf[0]) : 0.0;
+    if (out->fedf_i)
+      out->fedf_i[b] = tf[1] > 0 ? (double)fedf[(size_t)p.fedf_bins + b] / (fde * tf[1]) : 0.0;
+  }
+  // ion flux (reading C-21)
+  const double T = (double)steps * d.dt;
+  out->ion_flux_left = T > 0 ? (double)out->counters[kCnIAbsL] * W / (A * T) : 0.0;
+  out->ion_flux_right = T > 0 ? (double)out->counters[kCnIAbsR] * W / (A * T) : 0.0;
+  out->ion_flux = 0.5 * (out->ion_flux_left + out->ion_flux_right);
+  // centre density and temperature (reading C-19), criteria of §3.5
+  const double xc = 0.5 * nc;
+  const int j = (int)std::floor(xc);
+  const double f = xc - j;
+  const double n_c = (1 - f) * ne[j] + f * ne[std::min(j + 1, nc)];
+  const double ns = (double)out->counters[kCnEepfN];
+  const double mean_eps = ns > 0 ? ((double)out->counters[kCnEepfEsum] / 1048576.0) / ns : 0.0;
+  const double te = (2.0 / 3.0) * mean_eps;
+  out->n_e_center = n_c;
+  out->te_center_ev = te;
+  const double wfac = kQe * kQe / (kEps0 * kMe);
+  out->omega_pe_dt = std::sqrt(std::max(n_c, 0.0) * wfac) * d.dt;
+  const double nmax = *std::max_element(ne.begin(), ne.end());
+  out->omega_pe_dt_max = std::sqrt(std::max(nmax, 0.0) * wfac) * d.dt;
+  out->p_coll_e = d.pmax[0];
+  out->p_coll_i = d.pmax[1];
+  out->cfl_max = vmax * d.dt / d.dx;
+  const double lam = (n_c > 0 && te > 0) ? std::sqrt(kEps0 * te / (n_c * kQe)) : INFINITY;
+  out->lambda_d = lam;
+  out->dx_over_lambda_d = d.dx / lam;
+  out->n_debye = std::isfinite(lam) ? n_c * A * lam / W : INFINITY;  // reading C-20
+  if (rc != PIC_OK) return rc;
+  return out->omega_pe_dt_max > 2.0 ? PIC_WARN_UNSTABLE : PIC_OK;
+}
+
+void pic_free(pic_handle* h) { delete h; }
+
+const char* pic_strerror(int code) {
+  switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_ERR_PARAM: return "invalid parameter or argument";
+    case PIC_ERR_CUDA: return "CUDA error";
+    case PIC_ERR_CAPACITY: return "particle capacity exceeded (births dropped)";
+    case PIC_ERR_NONFINITE: return "non-finite particle velocity";
+    case PIC_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+    case PIC_WARN_UNSTABLE: return "omega_pe*dt above the leapfrog stability bound 2";
+    default: return "unknown code";
+  }
+}
+
+}  // extern "C"

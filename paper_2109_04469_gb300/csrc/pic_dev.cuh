@@ -1,0 +1,185 @@
+// pic_dev.cuh -- device-side layout and random-number / sampling helpers of libpic.
+//
+// Everything here implements the step contract of the PIC/MCC cycle of arXiv 2109.04469 §2
+// (readings C-16 and the sampling rules) for the CUDA path.  FP64 translation units that
+// include it are compiled with -fmad=false so every product and sum rounds exactly as
+// written (IEEE division and square root, no contraction).
+#pragma once
+#include <cstdint>
+
+namespace pic {
+
+constexpr int kChunk = 1024;       // particles per chunk (hole / birth bookkeeping unit)
+constexpr int kBlock = 256;        // threads per block of the particle kernels
+constexpr int kTile = 2 * kBlock;  // particles per block-wide pass (two per thread)
+constexpr int kXsNodes = 100001;   // collision table nodes at eps_k = k / 100 eV
+constexpr double kXsInvDe = 100.0;
+constexpr int kMaxTries = 64;      // rejection-sampling attempts before the fixed fallback
+constexpr int kNumCounters = 16;
+constexpr double kEExc = 11.55;    // eV, lumped excitation threshold
+constexpr double kEIon = 15.76;    // eV, ionization threshold (§3.1)
+
+enum : int { kStCapacity = 1, kStNonfinite = 2 };
+enum : int { kPurStep = 0, kPurColl = 1, kPurEmit = 2, kPurLoad = 3 };
+enum : int {
+  kCnEAbsL = 0, kCnEAbsR, kCnIAbsL, kCnIAbsR, kCnERefl, kCnSee, kCnEEla, kCnEExc, kCnEIon,
+  kCnIIso, kCnICx, kCnECand, kCnICand, kCnEepfN, kCnEepfEsum, kCnDropped
+};
+
+// Device-resident scalars that change every step.
+struct DevState {
+  long long n[2];       // live particles per species
+  long long n_snap[2];  // counts at the start of the current step's particle pass
+  unsigned next_id[2];  // next id per species (reading C-15)
+  unsigned step;        // step index n
+  unsigned step_next;   // n + 1, written by the particle pass for the compaction launch
+  int status;           // sticky kSt* bits
+  long long steps_avg;  // steps added to the RF-average accumulators
+  unsigned long long vmax_bits;  // scratch of the |vx| maximum reduction
+};
+
+// Everything a kernel needs, passed by value (constant bank).  Pointers address the
+// caller's workspace.
+struct DevCtx {
+  int nc, nx, steps_per_rf, eepf_bins, fedf_bins, nchunk_max;
+  long long cap;
+  double L, dx, inv_dx, inv_2dx, dt, efac, rfac, half_L, half_dx;
+  double qm_dt[2], emfac_e, spd2_e, emfac_rel, spd2_rel, emfac_ilab, mr2, sig_i, v_see;
+  double sig_load[2];
+  double pmax[2], refl, gamma, eepf_inv_de, fedf_inv_de;
+  // u < P_max  <=>  k < null_kthr for u = (2k+1) 2^-53 (exact integer threshold)
+  unsigned long long null_kthr[2];
+  int eepf_jlo, eepf_jhi;  // cells that can hold a particle of the EEPF window
+  unsigned key0, key1;
+  // particle state (FP64 path)
+  double *x[2], *vx[2], *vy[2], *vz[2];
+  unsigned *id[2];
+  // grid: counts C[buf][species][nx], potential, field, density accumulators [2][nx]
+  unsigned long long *C;
+  double *phi, *E, *acc;
+  const double *inv_den, *vtab, *F[2];
+  unsigned long long *eepf, *fedf, *counters;  // fedf [2][fedf_bins]
+  DevState *st;
+  // per-step scratch (hole / birth bookkeeping)
+  int *hole_idx[2];     // [cap]: holes of chunk c at c*kChunk + rank
+  int *hole_cnt[2];     // [nchunk_max]
+  int *eb_cnt[2];       // electron births per chunk of species s
+  int *ib_cnt;          // ion births per electron chunk
+  double *eb[2];        // [4][cap] records x, vx, vy, vz of electron births from species s
+  double *ib;           // [4][cap] ion births from electron chunks
+  int *hole_sorted[2];  // [cap] all holes of a species in ascending order
+};
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of the 4x32 Philox bijection with the
+// published round multipliers and Weyl key increments.
+struct U4 { unsigned a, b, c, d; };
+
+__device__ __forceinline__ U4 philox4x32_10(unsigned c0, unsigned c1, unsigned c2, unsigned c3,
+                                            unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// (2k+1) 2^-53 with k the top 52 bits of (hi, lo): strictly inside (0, 1)
+__device__ __forceinline__ double u52(unsigned hi, unsigned lo) {
+  const unsigned long long k = ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
+  return (double)(2ull * k + 1ull) * 0x1p-53;
+}
+
+// A counter-addressed stream: counter (id, step, species<<30 | purpose<<24 | block, 0).
+struct Stream {
+  unsigned k0, k1, id, step, base, block;
+  __device__ __forceinline__ Stream(const DevCtx& K, int species, int purpose, unsigned pid,
+                                    unsigned stp)
+      : k0(K.key0), k1(K.key1), id(pid), step(stp),
+        base(((unsigned)species << 30) | ((unsigned)purpose << 24)), block(0) {}
+  __device__ __forceinline__ void pair(double& ua, double& ub) {
+    const U4 w = philox4x32_10(id, step, base | block, 0u, k0, k1);
+    ++block;
+    ua = u52(w.a, w.b);
+    ub = u52(w.c, w.d);
+  }
+};
+
+// Natural logarithm of a positive normal double: binary exponent reduction to
+// m in [sqrt(1/2), sqrt(2)) and ln m = 2 artanh t, t = (m-1)/(m+1), summed to t^23.
+__device__ __forceinline__ double own_log(double x) {
+  const long long b = __double_as_longlong(x);
+  int k = (int)((b >> 52) & 0x7ff) - 1023;
+  double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+  if (m > 1.4142135623730951) {
+    m = m * 0.5;
+    k = k + 1;
+  }
+  const double t = (m - 1.0) / (m + 1.0);
+  const double t2 = t * t;
+  double s = 1.0 / 23.0;
+  s = s * t2 + 1.0 / 21.0;
+  s = s * t2 + 1.0 / 19.0;
+  s = s * t2 + 1.0 / 17.0;
+  s = s * t2 + 1.0 / 15.0;
+  s = s * t2 + 1.0 / 13.0;
+  s = s * t2 + 1.0 / 11.0;
+  s = s * t2 + 1.0 / 9.0;
+  s = s * t2 + 1.0 / 7.0;
+  s = s * t2 + 1.0 / 5.0;
+  s = s * t2 + 1.0 / 3.0;
+  s = s * t2 + 1.0;
+  return (double)k * 0.6931471805599453 + 2.0 * t * s;
+}
+
+// Marsaglia (1972): uniform direction by rejection of a point of the square.
+__device__ __forceinline__ void iso_dir(Stream& st, double& n0, double& n1, double& n2) {
+  for (int a = 0; a < kMaxTries; ++a) {
+    double ua, ub;
+    st.pair(ua, ub);
+    const double v1 = 2.0 * ua - 1.0, v2 = 2.0 * ub - 1.0;
+    const double s = v1 * v1 + v2 * v2;
+    if (s < 1.0) {
+      const double q = 2.0 * sqrt(1.0 - s);
+      n0 = v1 * q;
+      n1 = v2 * q;
+      n2 = 1.0 - 2.0 * s;
+      return;
+    }
+  }
+  n0 = 0.0; n1 = 0.0; n2 = 1.0;
+}
+
+// Marsaglia polar method: two independent standard normal deviates.
+__device__ __forceinline__ void gauss_pair(Stream& st, double& g0, double& g1) {
+  for (int a = 0; a < kMaxTries; ++a) {
+    double ua, ub;
+    st.pair(ua, ub);
+    const double v1 = 2.0 * ua - 1.0, v2 = 2.0 * ub - 1.0;
+    const double s = v1 * v1 + v2 * v2;
+    if (s < 1.0) {
+      const double fac = sqrt((-2.0 * own_log(s)) / s);
+      g0 = v1 * fac;
+      g1 = v2 * fac;
+      return;
+    }
+  }
+  g0 = 0.0; g1 = 0.0;
+}
+
+__device__ __forceinline__ void maxwell3(Stream& st, double sig, double& v0, double& v1,
+                                         double& v2) {
+  double a0, a1, b0, b1;
+  gauss_pair(st, a0, a1);
+  gauss_pair(st, b0, b1);
+  v0 = sig * a0;
+  v1 = sig * a1;
+  v2 = sig * b0;
+}
+
+}  // namespace pic

@@ -1,0 +1,27 @@
+// pic_launch.h -- host-side launchers of the libpic kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pic_dev.cuh"
+
+namespace pic {
+
+size_t field_smem_bytes(int nx);
+size_t push_smem_bytes(int nx);
+
+cudaError_t launch_init_load(const DevCtx& K, int species, long long n0, cudaStream_t s);
+cudaError_t launch_deposit(const DevCtx& K, int species, int buf, long long n, cudaStream_t s);
+// field of the current step from the current counts (no accumulation)
+cudaError_t launch_field(const DevCtx& K, cudaStream_t s);
+// particle pass of the current step
+cudaError_t launch_push_fp64(const DevCtx& K, int grid, cudaStream_t s);
+// compaction of the current step, accumulation, field of the next step, step += 1
+cudaError_t launch_compact_field(const DevCtx& K, cudaStream_t s);
+cudaError_t launch_set_step(const DevCtx& K, unsigned step, cudaStream_t s);
+cudaError_t launch_max_abs(const double* v, long long n, unsigned long long* out,
+                           cudaStream_t s);
+int push_fp64_blocks_per_sm(int nx);
+// raise the dynamic shared-memory limit of the grid-sized kernels for nx nodes
+cudaError_t configure_kernels(int nx);
+
+}  // namespace pic

@@ -1,0 +1,281 @@
+"""ctypes binding of libpic.so (C-ABI in include/pic.h).
+
+Argument marshalling only: every step of the PIC/MCC cycle (arXiv 2109.04469 §2 steps 1-6)
+runs in the library's CUDA kernels.  PyTorch provides the device workspace (one uint8
+tensor) and the CUDA stream.  There is no CPU fallback: if the library is missing or no
+GPU is present, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpic.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "pic.h")
+
+PIC_FP64, PIC_FP32 = 0, 1
+N_COUNTERS = 16
+XS_NODES = 100001
+ERRORS = {
+    -1: "PIC_ERR_PARAM", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_CAPACITY", -4: "PIC_ERR_NONFINITE",
+    -5: "PIC_ERR_WORKSPACE", 1: "PIC_WARN_UNSTABLE",
+}
+
+
+class PicParams(C.Structure):
+    _fields_ = [
+        ("gap_m", C.c_double), ("pressure_pa", C.c_double), ("gas_temp_k", C.c_double),
+        ("v_rf_amp_v", C.c_double), ("f_rf_hz", C.c_double),
+        ("steps_per_rf", C.c_int32), ("n_cells", C.c_int32),
+        ("weight", C.c_double), ("refl_e", C.c_double), ("gamma_see", C.c_double),
+        ("area_m2", C.c_double), ("init_te_ev", C.c_double), ("see_energy_ev", C.c_double),
+        ("init_per_species", C.c_int64), ("capacity_per_species", C.c_int64),
+        ("seed", C.c_uint64), ("instance", C.c_uint32), ("precision", C.c_int32),
+        ("eepf_bins", C.c_int32), ("eepf_emax_ev", C.c_double),
+        ("fedf_bins", C.c_int32), ("fedf_emax_ev", C.c_double),
+    ]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class PicDiagOut(C.Structure):
+    _fields_ = [
+        ("n_x", C.c_int32), ("eepf_bins", C.c_int32), ("fedf_bins", C.c_int32),
+        ("n_e", _DP), ("n_i", _DP), ("eepf_energy", _DP), ("eepf", _DP),
+        ("fedf_energy", _DP), ("fedf_e", _DP), ("fedf_i", _DP),
+        ("counters", C.c_uint64 * N_COUNTERS),
+        ("steps_averaged", C.c_int64), ("count_e", C.c_int64), ("count_i", C.c_int64),
+        ("ion_flux_left", C.c_double), ("ion_flux_right", C.c_double), ("ion_flux", C.c_double),
+        ("n_e_center", C.c_double), ("te_center_ev", C.c_double),
+        ("omega_pe_dt", C.c_double), ("omega_pe_dt_max", C.c_double),
+        ("p_coll_e", C.c_double), ("p_coll_i", C.c_double), ("cfl_max", C.c_double),
+        ("lambda_d", C.c_double), ("dx_over_lambda_d", C.c_double), ("n_debye", C.c_double),
+        ("status", C.c_int32),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of the entry points declared in include/pic.h."""
+    src = open(HEADER).read()
+    return re.findall(r"^\s*(?:int|void|const char\*)\s+(pic_\w+)\s*\(", src, re.M)
+
+
+def lib() -> C.CDLL:
+    """Load libpic.so (raises if it was not built: the product has no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build()")
+            L = C.CDLL(LIB_PATH)
+            P, i64, u32 = C.c_void_p, C.c_int64, C.c_uint32
+            sig = {
+                "pic_workspace_bytes": (C.c_int, [C.POINTER(PicParams), C.POINTER(C.c_size_t)]),
+                "pic_init": (C.c_int, [C.POINTER(PicParams), P, C.c_size_t, P, C.POINTER(P)]),
+                "pic_step": (C.c_int, [P, i64]),
+                "pic_sync": (C.c_int, [P]),
+                "pic_step_profiled": (C.c_int, [P, i64, P]),
+                "pic_diag": (C.c_int, [P, C.POINTER(PicDiagOut)]),
+                "pic_get_particles": (C.c_int, [P, C.c_int, P, P, P, P, P, i64, C.POINTER(i64)]),
+                "pic_set_particles": (C.c_int, [P, C.c_int, P, P, P, P, P, i64, u32]),
+                "pic_counts": (C.c_int, [P, C.POINTER(i64), C.POINTER(i64)]),
+                "pic_get_grid": (C.c_int, [P, P, P, P, P]),
+                "pic_solve_field": (C.c_int, [P]),
+                "pic_get_accum": (C.c_int, [P, P, P, P, P, P, P, C.POINTER(i64)]),
+                "pic_reset_averages": (C.c_int, [P]),
+                "pic_set_step": (C.c_int, [P, u32]),
+                "pic_get_step": (C.c_int, [P, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
+                "pic_override_table": (C.c_int, [P, C.c_int, P, C.c_double]),
+                "pic_get_derived": (C.c_int, [P, P]),
+                "pic_free": (None, [P]),
+                "pic_strerror": (C.c_char_p, [C.c_int]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = lib().pic_strerror(code).decode() if _lib else ERRORS.get(code, str(code))
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({msg})")
+
+
+def _check(code: int, what: str, allow_warn: bool = True) -> int:
+    if code < 0 or (code > 0 and not allow_warn):
+        raise PicError(code, what)
+    return code
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+DEFAULTS = dict(
+    gas_temp_k=300.0, f_rf_hz=13.56e6, area_m2=1e-4, init_te_ev=3.0, see_energy_ev=1.0,
+    refl_e=0.0, gamma_see=0.0, seed=1, instance=0, precision=PIC_FP64, eepf_bins=500,
+    eepf_emax_ev=50.0, fedf_bins=500, fedf_emax_ev=500.0,
+)
+
+
+def make_params(cfg: dict) -> PicParams:
+    d = dict(DEFAULTS)
+    d.update(cfg)
+    p = PicParams()
+    for name, _ in PicParams._fields_:
+        setattr(p, name, d[name])
+    return p
+
+
+def workspace_bytes(cfg: dict) -> int:
+    p = make_params(cfg)
+    n = C.c_size_t(0)
+    _check(lib().pic_workspace_bytes(C.byref(p), C.byref(n)), "pic_workspace_bytes")
+    return n.value
+
+
+class Simulation:
+    """One simulation on the current CUDA device and torch's current stream."""
+
+    def __init__(self, cfg: dict, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpic needs a CUDA device; there is no CPU path")
+        self.cfg = dict(DEFAULTS)
+        self.cfg.update(cfg)
+        self._p = make_params(self.cfg)
+        nbytes = workspace_bytes(self.cfg)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib().pic_init(C.byref(self._p), C.c_void_p(self.workspace.data_ptr()), nbytes,
+                              C.c_void_p(self.stream.cuda_stream), C.byref(h)), "pic_init")
+        self._h = h
+        self.nx = self.cfg["n_cells"] + 1
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().pic_free(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, n: int = 1) -> int:
+        return _check(lib().pic_step(self._h, int(n)), "pic_step")
+
+    def step_profiled(self, n: int, ms: np.ndarray) -> int:
+        """n steps with per-launch CUDA-event times added to ms[0] (particle pass) and ms[1]
+        (compaction with the next field solve beside it)."""
+        assert ms.dtype == np.float64 and ms.shape == (2,)
+        return _check(lib().pic_step_profiled(self._h, int(n), _ptr(ms)), "pic_step_profiled")
+
+    def sync(self) -> int:
+        return _check(lib().pic_sync(self._h), "pic_sync")
+
+    def status(self) -> int:
+        return lib().pic_sync(self._h)
+
+    def counts(self) -> tuple[int, int]:
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib().pic_counts(self._h, C.byref(a), C.byref(b)), "pic_counts")
+        return a.value, b.value
+
+    def step_state(self) -> tuple[int, int, int]:
+        s, e, i = C.c_uint32(), C.c_uint32(), C.c_uint32()
+        _check(lib().pic_get_step(self._h, C.byref(s), C.byref(e), C.byref(i)), "pic_get_step")
+        return s.value, e.value, i.value
+
+    def particles(self, s: int) -> dict:
+        n = self.counts()[s]
+        out = {k: np.zeros(n) for k in ("x", "vx", "vy", "vz")}
+        out["id"] = np.zeros(n, dtype=np.uint32)
+        got = C.c_int64()
+        _check(lib().pic_get_particles(self._h, s, _ptr(out["x"]), _ptr(out["vx"]),
+                                       _ptr(out["vy"]), _ptr(out["vz"]), _ptr(out["id"]), n,
+                                       C.byref(got)), "pic_get_particles")
+        return out
+
+    def set_particles(self, s: int, x, vx, vy, vz, ids, next_id: int):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, vx, vy, vz)]
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        _check(lib().pic_set_particles(self._h, s, *[_ptr(a) for a in arrs], _ptr(ids),
+                                       len(ids), next_id), "pic_set_particles")
+
+    def grid(self) -> dict:
+        g = dict(Ce=np.zeros(self.nx, np.int64), Ci=np.zeros(self.nx, np.int64),
+                 phi=np.zeros(self.nx), E=np.zeros(self.nx))
+        _check(lib().pic_get_grid(self._h, _ptr(g["Ce"]), _ptr(g["Ci"]), _ptr(g["phi"]),
+                                  _ptr(g["E"])), "pic_get_grid")
+        return g
+
+    def solve_field(self):
+        _check(lib().pic_solve_field(self._h), "pic_solve_field")
+
+    def accum(self) -> dict:
+        c = self.cfg
+        a = dict(acc_e=np.zeros(self.nx), acc_i=np.zeros(self.nx),
+                 eepf=np.zeros(c["eepf_bins"], np.uint64),
+                 fedf_e=np.zeros(c["fedf_bins"], np.uint64),
+                 fedf_i=np.zeros(c["fedf_bins"], np.uint64),
+                 counters=np.zeros(N_COUNTERS, np.uint64))
+        st = C.c_int64()
+        _check(lib().pic_get_accum(self._h, _ptr(a["acc_e"]), _ptr(a["acc_i"]), _ptr(a["eepf"]),
+                                   _ptr(a["fedf_e"]), _ptr(a["fedf_i"]), _ptr(a["counters"]),
+                                   C.byref(st)), "pic_get_accum")
+        a["steps"] = st.value
+        return a
+
+    def reset_averages(self):
+        _check(lib().pic_reset_averages(self._h), "pic_reset_averages")
+
+    def set_step(self, n: int):
+        _check(lib().pic_set_step(self._h, n), "pic_set_step")
+
+    def override_table(self, s: int, F: np.ndarray, numax: float):
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        assert F.shape == (XS_NODES, 4)
+        _check(lib().pic_override_table(self._h, s, _ptr(F), float(numax)), "pic_override_table")
+
+    def derived(self) -> dict:
+        out = np.zeros(7)
+        _check(lib().pic_get_derived(self._h, _ptr(out)), "pic_get_derived")
+        return dict(zip(("dt", "dx", "ng", "numax_e", "numax_i", "pmax_e", "pmax_i"),
+                        out.tolist()))
+
+    def diag(self) -> dict:
+        c = self.cfg
+        arrs = dict(n_e=np.zeros(self.nx), n_i=np.zeros(self.nx),
+                    eepf_energy=np.zeros(c["eepf_bins"]), eepf=np.zeros(c["eepf_bins"]),
+                    fedf_energy=np.zeros(c["fedf_bins"]), fedf_e=np.zeros(c["fedf_bins"]),
+                    fedf_i=np.zeros(c["fedf_bins"]))
+        d = PicDiagOut()
+        d.n_x, d.eepf_bins, d.fedf_bins = self.nx, c["eepf_bins"], c["fedf_bins"]
+        for k, a in arrs.items():
+            setattr(d, k, a.ctypes.data_as(_DP))
+        rc = _check(lib().pic_diag(self._h, C.byref(d)), "pic_diag")
+        out = dict(arrs)
+        for name, _ in PicDiagOut._fields_:
+            if name in arrs or name in ("n_x", "eepf_bins", "fedf_bins"):
+                continue
+            v = getattr(d, name)
+            out[name] = np.array(v[:], dtype=np.uint64) if name == "counters" else v
+        out["return_code"] = rc
+        return out
