@@ -98,6 +98,7 @@ def lib():
             L.orc_override_table.argtypes = [P, C.c_int, P, C.c_double]
             L.orc_get_table.argtypes = [P, C.c_int, P]
             L.orc_set_counts.argtypes = [P, P, P]
+            L.orc_thomas_phi.argtypes = [P, C.c_double, P]
             L.orc_philox4x32_10.argtypes = [P, P, P]
             L.orc_log.restype = C.c_double
             L.orc_log.argtypes = [C.c_double]
@@ -231,6 +232,12 @@ class OracleSim:
         Ci = np.ascontiguousarray(Ci, dtype=np.int64)
         assert Ce.shape == (self.nx,) and Ci.shape == (self.nx,)
         lib().orc_set_counts(self._h, _ptr(Ce), _ptr(Ci))
+
+    def thomas_phi(self, V: float) -> np.ndarray:
+        """Potential of the current counts by the Thomas algorithm (pin of the field solve)."""
+        out = np.zeros(self.nx)
+        lib().orc_thomas_phi(self._h, float(V), _ptr(out))
+        return out
 
     def solve_field(self):
         lib().orc_solve_field(self._h)

@@ -63,7 +63,7 @@ typedef struct {
   /* derived (§2, DESIGN contract 2.1) */
   int nc, nx;
   double dx, inv_dx, inv_2dx, dt, ng, qm_dt[2], emfac_e, spd2_e, mu, emfac_rel, spd2_rel,
-      emfac_ilab, mr2, sig_e, sig_i, v_see, efac, rfac, mass[2];
+      emfac_ilab, mr2, sig_e, sig_i, v_see, efac, rfac, den1, den2, mass[2];
   double *inv_den; /* Poisson pivots, index 1..nc-1 */
   double *vtab;    /* drive table, N_t entries */
   double *F[2];    /* cumulative collision fractions, XS_NODES x 4 */
@@ -328,14 +328,14 @@ static void deposit(const orc_sim *S, int64_t *C, double x) {
 }
 
 /* ----------------------------------------------------------------- field (§2 step 2) */
-static void field(orc_sim *S, double V, int accumulate) {
+/* The Thomas algorithm named in §2 step 2, on the constant tridiagonal matrix (-1, 2, -1)
+ * with pivots precomputed: kept as the pin of field() below (both solve the same system). */
+void orc_thomas_phi(const orc_sim *S, double V, double *phi) {
   int nc = S->nc;
   const int64_t *Ce = S->C[SP_E], *Ci = S->C[SP_I];
   double *g = (double *)malloc(sizeof(double) * (size_t)(nc + 1));
-  double *phi = S->phi;
   phi[0] = V;
   phi[nc] = 0.0;
-  /* Thomas algorithm on the constant tridiagonal matrix (-1, 2, -1), pivots precomputed */
   for (int j = 1; j <= nc - 1; ++j) {
     double r = (double)(Ci[j] - Ce[j]) * S->rfac;
     if (j == 1)
@@ -350,12 +350,44 @@ static void field(orc_sim *S, double V, int accumulate) {
       phi[j] = g[j] + S->inv_den[j] * phi[j + 1];
   }
   free(g);
-  double *E = S->E;
-  for (int j = 1; j <= nc - 1; ++j) E[j] = (phi[j - 1] - phi[j + 1]) * S->inv_2dx;
-  E[0] = (phi[0] - phi[1]) * S->inv_dx - (double)(Ci[0] - Ce[0]) * S->efac;
-  E[nc] = (phi[nc - 1] - phi[nc]) * S->inv_dx + (double)(Ci[nc] - Ce[nc]) * S->efac;
+}
+
+/* §2 step 2 (reading C-23).  The finite-difference system 2 phi_j - phi_{j-1} - phi_{j+1} =
+ * r_j (j = 1..N-1), phi_0 = V, phi_N = 0, r_j = rfac (C_i,j - C_e,j), has the solution
+ *   phi_j = V (N-j)/N + sum_k G(j,k) r_k,  G(j,k) = min(j,k) (N - max(j,k)) / N
+ * (the discrete Green's function of the Dirichlet matrix).  With integer counts,
+ *   S_j = N sum_k G(j,k) dC_k = (N-j) sum_{k<=j} k dC_k + j sum_{k>j} (N-k) dC_k
+ * is an exact integer, so phi_j = (V (N-j) + rfac S_j) / N rounds once.  The field follows
+ * from the same exact sums: E_j = N(phi_{j-1} - phi_{j+1}) / (2 N dx) inside, and the
+ * half-cell Gauss law at the electrodes (reading C-4). */
+static void field(orc_sim *S, double V, int accumulate) {
+  const int N = S->nc;
+  const int64_t *Ce = S->C[SP_E], *Ci = S->C[SP_I];
+  __int128 *A = (__int128 *)malloc(sizeof(__int128) * (size_t)(N + 1));
+  __int128 *B = (__int128 *)malloc(sizeof(__int128) * (size_t)(N + 1));
+  __int128 *Sg = (__int128 *)malloc(sizeof(__int128) * (size_t)(N + 1));
+  A[0] = 0;
+  for (int k = 1; k <= N - 1; ++k) A[k] = A[k - 1] + (__int128)k * (__int128)(Ci[k] - Ce[k]);
+  A[N] = A[N - 1];
+  B[N] = 0;
+  B[N - 1] = 0;
+  for (int k = N - 2; k >= 0; --k)
+    B[k] = B[k + 1] + (__int128)(N - (k + 1)) * (__int128)(Ci[k + 1] - Ce[k + 1]);
+  for (int j = 0; j <= N; ++j) Sg[j] = (__int128)(N - j) * A[j] + (__int128)j * B[j];
+  double *phi = S->phi, *E = S->E;
+  phi[0] = V;
+  phi[N] = 0.0;
+  for (int j = 1; j <= N - 1; ++j)
+    phi[j] = (V * (double)(N - j) + S->rfac * (double)Sg[j]) / (double)N;
+  for (int j = 1; j <= N - 1; ++j)
+    E[j] = (2.0 * V + S->rfac * (double)(Sg[j - 1] - Sg[j + 1])) / S->den2;
+  E[0] = (V - S->rfac * (double)(Sg[1] + (__int128)N * (__int128)(Ci[0] - Ce[0]))) / S->den1;
+  E[N] = (V + S->rfac * (double)(Sg[N - 1] + (__int128)N * (__int128)(Ci[N] - Ce[N]))) / S->den1;
+  free(A);
+  free(B);
+  free(Sg);
   if (accumulate) {
-    for (int j = 0; j <= nc; ++j) {
+    for (int j = 0; j <= N; ++j) {
       S->acc[SP_E][j] += (double)Ce[j];
       S->acc[SP_I][j] += (double)Ci[j];
     }
@@ -389,6 +421,8 @@ static void derive(orc_sim *S) {
   S->v_see = sqrt(p->see_energy_ev * S->spd2_e);
   S->efac = (Q_E * p->weight) / ((p->area_m2 * EPS_0) * TWO32);
   S->rfac = S->efac * S->dx;
+  S->den1 = S->dx * (double)S->nc;
+  S->den2 = (2.0 * S->dx) * (double)S->nc;
   S->inv_den = (double *)calloc((size_t)S->nc + 1, sizeof(double));
   double den = 2.0;
   for (int j = 1; j <= S->nc - 1; ++j) {

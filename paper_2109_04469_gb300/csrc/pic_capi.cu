@@ -277,6 +277,8 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   K.dt = d.dt;
   K.efac = d.efac;
   K.rfac = d.rfac;
+  K.den1 = d.dx * (double)nc;  // N dx and 2 N dx of the field solve (reading C-23)
+  K.den2 = (2.0 * d.dx) * (double)nc;
   K.half_L = 0.5 * p->gap_m;
   K.half_dx = 0.5 * d.dx;
   K.qm_dt[0] = d.qm_dt[0];

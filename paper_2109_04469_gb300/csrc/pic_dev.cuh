@@ -43,7 +43,7 @@ struct DevState {
 struct DevCtx {
   int nc, nx, steps_per_rf, eepf_bins, fedf_bins, nchunk_max;
   long long cap;
-  double L, dx, inv_dx, inv_2dx, dt, efac, rfac, half_L, half_dx;
+  double L, dx, inv_dx, inv_2dx, dt, efac, rfac, den1, den2, half_L, half_dx;
   double qm_dt[2], emfac_e, spd2_e, emfac_rel, spd2_rel, emfac_ilab, mr2, sig_i, v_see;
   double sig_load[2];
   double pmax[2], refl, gamma, eepf_inv_de, fedf_inv_de;

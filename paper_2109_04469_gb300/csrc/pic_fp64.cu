@@ -148,86 +148,149 @@ __global__ void k_max_abs(const double* __restrict__ v, long long n, unsigned lo
 }
 
 // ------------------------------------------------------------------- field (§2 step 2)
-// Counts of buffer `buf` -> right-hand side (all threads) -> Thomas sweeps (pivots 1/den_j of
-// the constant matrix tridiag(-1, 2, -1), precomputed on the host and staged in shared
-// memory; one thread, the recursion is serial) -> E by differencing (all threads).
-// smem: 4 * nx doubles.
+// Round-to-nearest-even conversion of a 128-bit integer to double (the one rounding of each
+// field value).
+__device__ __forceinline__ double i128_to_f64(__int128 v) {
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  const unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  if (msb <= 52) {
+    const double d = (double)lo;  // exact
+    return neg ? -d : d;
+  }
+  int sh = msb - 52;
+  unsigned long long mant = (unsigned long long)(u >> sh);  // 53 significant bits
+  const unsigned __int128 rem = u - ((unsigned __int128)mant << sh);
+  const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+  if (rem > half || (rem == half && (mant & 1ull))) {
+    ++mant;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++sh;
+    }
+  }
+  const unsigned long long bits =
+      ((unsigned long long)(sh + 52 + 1023) << 52) | (mant & ((1ull << 52) - 1ull));
+  const double d = __longlong_as_double((long long)bits);
+  return neg ? -d : d;
+}
+
+__device__ __forceinline__ __int128 shfl_up_i128(__int128 v, int o) {
+  unsigned long long lo = (unsigned long long)v;
+  unsigned long long hi = (unsigned long long)((unsigned __int128)v >> 64);
+  lo = __shfl_up_sync(0xffffffffu, lo, o);
+  hi = __shfl_up_sync(0xffffffffu, hi, o);
+  return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+
+// Exclusive block scan of two int128 values (exact: integer sums are order-free).
+__device__ __forceinline__ void block_scan_i128x2(__int128& a, __int128& b, __int128& ta,
+                                                  __int128& tb) {
+  __shared__ __int128 wa[33], wb[33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __int128 ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const __int128 ya = shfl_up_i128(ia, o), yb = shfl_up_i128(ib, o);
+    if (lane >= o) {
+      ia += ya;
+      ib += yb;
+    }
+  }
+  if (lane == 31) {
+    wa[w] = ia;
+    wb[w] = ib;
+  }
+  __syncthreads();
+  if (w == 0) {
+    __int128 xa = (lane < nw) ? wa[lane] : (__int128)0, xb = (lane < nw) ? wb[lane] : (__int128)0;
+    __int128 sa = xa, sb = xb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const __int128 ya = shfl_up_i128(sa, o), yb = shfl_up_i128(sb, o);
+      if (lane >= o) {
+        sa += ya;
+        sb += yb;
+      }
+    }
+    if (lane < nw) {
+      wa[lane] = sa - xa;
+      wb[lane] = sb - xb;
+    }
+    if (lane == nw - 1) {
+      wa[32] = sa;
+      wb[32] = sb;
+    }
+  }
+  __syncthreads();
+  const __int128 ea = wa[w] + ia - a, eb = wb[w] + ib - b;
+  ta = wa[32];
+  tb = wb[32];
+  __syncthreads();
+  a = ea;
+  b = eb;
+}
+
+// Field of step `step` from the counts of buffer `buf` (reading C-23): the tridiagonal
+// system of §2 step 2 solved through its discrete Green's function,
+//   S_j = (N-j) sum_{k<=j} k dC_k + j sum_{k>j} (N-k) dC_k   (exact int128 prefix sums),
+//   phi_j = (V (N-j) + rfac S_j) / N,
+//   E_j = (2V + rfac (S_{j-1} - S_{j+1})) / (2 N dx)   inside,
+//   E_0 = (V - rfac (S_1 + N dC_0)) / (N dx),  E_N = (V + rfac (S_{N-1} + N dC_N)) / (N dx)
+// (half-cell Gauss law at the electrodes, reading C-4).  Each value rounds once, so the
+// result is independent of the thread count.  smem: 16 * nx bytes.
 __device__ __forceinline__ void field_solve(const DevCtx& K, unsigned step, int buf,
-                                            double* smem) {
-  const int nc = K.nc, nx = K.nx;
-  double* r = smem;
-  double* g = r + nx;
-  double* phi = g + nx;
-  double* inv = phi + nx;
+                                            void* smem) {
+  const int N = K.nc, nx = K.nx;
+  __int128* Sg = reinterpret_cast<__int128*>(smem);
   const unsigned long long* Ce = K.C + (size_t)(buf * 2 + 0) * nx;
   const unsigned long long* Ci = K.C + (size_t)(buf * 2 + 1) * nx;
   const double V = K.vtab[step % (unsigned)K.steps_per_rf];  // reading C-2
+  const int seg = (nx + blockDim.x - 1) / blockDim.x;
+  const int j0 = min((int)threadIdx.x * seg, nx), j1 = min(j0 + seg, nx);
+  __int128 sa = 0, sb = 0;
+  for (int j = j0; j < j1; ++j)
+    if (j >= 1 && j <= N - 1) {
+      const long long dc = (long long)Ci[j] - (long long)Ce[j];
+      sa += (__int128)j * dc;
+      sb += (__int128)(N - j) * dc;
+    }
+  __int128 ta, tb;
+  block_scan_i128x2(sa, sb, ta, tb);
+  for (int j = j0; j < j1; ++j) {
+    if (j >= 1 && j <= N - 1) {
+      const long long dc = (long long)Ci[j] - (long long)Ce[j];
+      sa += (__int128)j * dc;
+      sb += (__int128)(N - j) * dc;
+    }
+    Sg[j] = (__int128)(N - j) * sa + (__int128)j * (tb - sb);
+  }
+  __syncthreads();
   for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-    r[j] = (double)((long long)Ci[j] - (long long)Ce[j]) * K.rfac;
-    inv[j] = K.inv_den[j];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double gp = (r[1] + V) * inv[1];
-    g[1] = gp;
-    int j = 2;
-    for (; j + 3 <= nc - 1; j += 4) {
-      const double r0 = r[j], r1 = r[j + 1], r2 = r[j + 2], r3 = r[j + 3];
-      const double i0 = inv[j], i1 = inv[j + 1], i2 = inv[j + 2], i3 = inv[j + 3];
-      gp = (r0 + gp) * i0;
-      g[j] = gp;
-      gp = (r1 + gp) * i1;
-      g[j + 1] = gp;
-      gp = (r2 + gp) * i2;
-      g[j + 2] = gp;
-      gp = (r3 + gp) * i3;
-      g[j + 3] = gp;
+    double e, ph;
+    if (j == 0) {
+      const __int128 q = Sg[1] + (__int128)N * (__int128)((long long)Ci[0] - (long long)Ce[0]);
+      e = (V - K.rfac * i128_to_f64(q)) / K.den1;
+      ph = V;
+    } else if (j == N) {
+      const __int128 q = Sg[N - 1] + (__int128)N * (__int128)((long long)Ci[N] - (long long)Ce[N]);
+      e = (V + K.rfac * i128_to_f64(q)) / K.den1;
+      ph = 0.0;
+    } else {
+      e = (2.0 * V + K.rfac * i128_to_f64(Sg[j - 1] - Sg[j + 1])) / K.den2;
+      ph = (V * (double)(N - j) + K.rfac * i128_to_f64(Sg[j])) / (double)N;
     }
-    for (; j <= nc - 1; ++j) {
-      gp = (r[j] + gp) * inv[j];
-      g[j] = gp;
-    }
-    double ph = gp;
-    phi[nc - 1] = ph;
-    j = nc - 2;
-    for (; j - 3 >= 1; j -= 4) {
-      const double g0 = g[j], g1 = g[j - 1], g2 = g[j - 2], g3 = g[j - 3];
-      const double i0 = inv[j], i1 = inv[j - 1], i2 = inv[j - 2], i3 = inv[j - 3];
-      ph = g0 + i0 * ph;
-      phi[j] = ph;
-      ph = g1 + i1 * ph;
-      phi[j - 1] = ph;
-      ph = g2 + i2 * ph;
-      phi[j - 2] = ph;
-      ph = g3 + i3 * ph;
-      phi[j - 3] = ph;
-    }
-    for (; j >= 1; --j) {
-      ph = g[j] + inv[j] * ph;
-      phi[j] = ph;
-    }
-    phi[0] = V;
-    phi[nc] = 0.0;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j <= nc; j += blockDim.x) {
-    double e;
-    if (j == 0)
-      e = (phi[0] - phi[1]) * K.inv_dx - (double)((long long)Ci[0] - (long long)Ce[0]) * K.efac;
-    else if (j == nc)
-      e = (phi[nc - 1] - phi[nc]) * K.inv_dx +
-          (double)((long long)Ci[nc] - (long long)Ce[nc]) * K.efac;
-    else
-      e = (phi[j - 1] - phi[j + 1]) * K.inv_2dx;
     K.E[j] = e;
-    K.phi[j] = phi[j];
+    K.phi[j] = ph;
   }
 }
 
 // Stand-alone solve for the current step (after init, set_particles, set_step, or on
 // request); touches no accumulator.
 __global__ void k_field(DevCtx K) {
-  extern __shared__ double fsm[];
+  extern __shared__ __align__(16) unsigned char fsm[];
   const unsigned step = K.st->step;
   field_solve(K, step, step & 1, fsm);
 }
@@ -670,7 +733,7 @@ __device__ void compact_species(const DevCtx& K, int s, int* sPref, int* sCnt, i
 
 // Block 2: close step n's accumulation (acc += C(n), counted) and clear that buffer for the
 // deposit of step n+1, then solve the field of step n+1.
-__device__ void advance_field(const DevCtx& K, double* smem) {
+__device__ void advance_field(const DevCtx& K, void* smem) {
   const unsigned m = K.st->step_next;  // n + 1
   const int done = (m - 1u) & 1u;      // buffer of step n
   const int nx = K.nx;
@@ -686,7 +749,7 @@ __device__ void advance_field(const DevCtx& K, double* smem) {
 }
 
 __global__ void __launch_bounds__(kCompactThreads) k_compact_field(DevCtx K) {
-  extern __shared__ double csm[];
+  extern __shared__ __align__(16) unsigned char csm[];
   __shared__ int sPref[kCompactThreads], sCnt[kCompactThreads];
   __shared__ int sWarp[kCompactThreads / 32 + 1];
   if (blockIdx.x < 2) {
@@ -698,7 +761,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact_field(DevCtx K) {
 }
 
 // ------------------------------------------------------------------------ launchers
-size_t field_smem_bytes(int nx) { return sizeof(double) * 4 * (size_t)nx; }
+size_t field_smem_bytes(int nx) { return sizeof(__int128) * (size_t)nx; }
 size_t push_smem_bytes(int nx) {
   return sizeof(double) * (size_t)nx + sizeof(unsigned long long) * (2 * (size_t)nx + kNumCounters);
 }

@@ -94,6 +94,58 @@ def test_discrete_gauss_law(nc):
     assert abs((E[-1] - E[0]) - q_per_area / EPS0) <= 1e-9 * abs(q_per_area / EPS0)
 
 
+@pytest.mark.parametrize("nc", [2, 3, 17, 400, 4096])
+def test_green_function_solve_matches_thomas(nc):
+    """The exact Green's-function evaluation (reading C-23) and the Thomas algorithm named in
+    §2 step 2 solve the same tridiagonal system: they agree to rounding."""
+    s = _sim(n_cells=nc, v_rf_amp_v=-61.0, weight=3e5)
+    Ce, Ci = _random_counts(nc, 7 * nc)
+    s.set_counts(Ce, Ci)
+    s.solve_field()
+    phi = s.grid()["phi"]
+    th = s.thomas_phi(-61.0)
+    # the sequential sweep's rounding grows with the condition number (~nc^2) of the matrix
+    tol = max(1e-13, 2.2e-16 * nc * nc)
+    assert np.max(np.abs(phi - th)) <= tol * max(np.max(np.abs(th)), 61.0)
+
+
+def test_green_function_solve_exact_rational():
+    """On a small grid the solve is compared with an exact rational solution (fractions)
+    of the tridiagonal system: the only error left is the final rounding."""
+    from fractions import Fraction as Fr
+
+    nc, V = 9, 37.0
+    s = _sim(n_cells=nc, v_rf_amp_v=V, weight=4e5)
+    Ce, Ci = _random_counts(nc, 3)
+    s.set_counts(Ce, Ci)
+    s.solve_field()
+    phi = s.grid()["phi"]
+    rfac = Fr(s.derived()["rfac"])
+    # Gaussian elimination in exact arithmetic
+    M = nc - 1
+    a = [[Fr(0)] * M for _ in range(M)]
+    b = [rfac * int(Ci[j + 1] - Ce[j + 1]) for j in range(M)]
+    b[0] += Fr(V)
+    for i in range(M):
+        a[i][i] = Fr(2)
+        if i:
+            a[i][i - 1] = Fr(-1)
+        if i + 1 < M:
+            a[i][i + 1] = Fr(-1)
+    for i in range(M):
+        for r in range(i + 1, M):
+            f = a[r][i] / a[i][i]
+            for c in range(i, M):
+                a[r][c] -= f * a[i][c]
+            b[r] -= f * b[i]
+    x = [Fr(0)] * M
+    for i in reversed(range(M)):
+        x[i] = (b[i] - sum(a[i][c] * x[c] for c in range(i + 1, M))) / a[i][i]
+    for j in range(M):
+        exact = x[j]
+        assert abs(Fr(phi[j + 1]) - exact) <= abs(exact) * Fr(2, 2**52) + Fr(1, 2**60)
+
+
 def test_field_is_linear_in_charge_and_voltage():
     s = _sim(n_cells=50, v_rf_amp_v=10.0)
     Ce, Ci = _random_counts(50, 9)
