@@ -176,14 +176,18 @@ void carve(const pic_params& p, char* base, DevCtx& K, size_t* total) {
   K.eepf = c.take<unsigned long long>((size_t)p.eepf_bins);
   K.fedf = c.take<unsigned long long>((size_t)2 * p.fedf_bins);
   K.counters = c.take<unsigned long long>(kNumCounters);
+  // per-block list counts: any particle grid has at most 2 * nch blocks
+  const size_t nl = (size_t)2 * nch + 8;
   for (int s = 0; s < 2; ++s) {
     K.hole_idx[s] = c.take<int>(cap);
-    K.hole_cnt[s] = c.take<int>(nch);
-    K.eb_cnt[s] = c.take<int>(nch);
+    K.hole_cnt[s] = c.take<int>(nl);
+    K.hole_pref[s] = c.take<int>(nl);
+    K.eb_cnt[s] = c.take<int>(nl);
+    K.eb_pref[s] = c.take<int>(nl);
     K.eb[s] = c.take<double>(4 * cap);
-    K.hole_sorted[s] = c.take<int>(cap);
   }
-  K.ib_cnt = c.take<int>(nch);
+  K.ib_cnt = c.take<int>(nl);
+  K.ib_pref = c.take<int>(nl);
   K.ib = c.take<double>(4 * cap);
   *total = (c.off + 255) & ~size_t(255);
 }
@@ -211,6 +215,7 @@ struct pic_handle {
   char* ws;
   size_t ws_bytes;
   int push_grid;
+  int place_grid;
   int last_status;
 };
 
@@ -321,6 +326,9 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
     return fail(PIC_ERR_CUDA);
   const int bps = push_fp64_blocks_per_sm(nx);
   h->push_grid = std::max(1, std::min(2 * K.nchunk_max, sms * bps));
+  h->place_grid = 1 + sms;
+  K.nlist = h->push_grid;
+  h->K.nlist = h->push_grid;
 
   DevState s0;
   std::memset(&s0, 0, sizeof s0);
@@ -353,7 +361,7 @@ int pic_step(pic_handle* h, int64_t n_steps) {
   if (!h || n_steps < 0) return PIC_ERR_PARAM;
   for (int64_t i = 0; i < n_steps; ++i) {
     if (launch_push_fp64(h->K, h->push_grid, h->stream) != cudaSuccess ||
-        launch_compact_field(h->K, h->stream) != cudaSuccess) {
+        launch_place_fp64(h->K, h->place_grid, h->stream) != cudaSuccess) {
       (void)cudaGetLastError();
       return PIC_ERR_CUDA;
     }
@@ -376,7 +384,7 @@ int pic_step_profiled(pic_handle* h, int64_t n_steps, double* ms_out) {
     if (cudaEventRecord(ev[0], h->stream) != cudaSuccess ||
         launch_push_fp64(h->K, h->push_grid, h->stream) != cudaSuccess ||
         cudaEventRecord(ev[1], h->stream) != cudaSuccess ||
-        launch_compact_field(h->K, h->stream) != cudaSuccess ||
+        launch_place_fp64(h->K, h->place_grid, h->stream) != cudaSuccess ||
         cudaEventRecord(ev[2], h->stream) != cudaSuccess ||
         cudaEventSynchronize(ev[2]) != cudaSuccess ||
         cudaEventElapsedTime(&t[0], ev[0], ev[1]) != cudaSuccess ||

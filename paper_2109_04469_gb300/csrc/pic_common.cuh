@@ -1,0 +1,408 @@
+// pic_common.cuh -- precision-independent device code of libpic: block scans, the exact field
+// solve of §2 step 2 (reading C-23), the hole / birth bookkeeping of the compaction (reading
+// C-15) and the placement launch.  Included by the FP64 and FP32 translation units; the FP64
+// arithmetic here uses explicit round-to-nearest intrinsics so no compiler flag can contract
+// it into fused multiply-adds.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pic_dev.cuh"
+
+namespace pic {
+
+template <int NW>
+__device__ __forceinline__ int block_excl_scan(int v, int* sWarp, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) sWarp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const int t = (lane < NW) ? sWarp[lane] : 0;
+    int ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += y;
+    }
+    if (lane < NW) sWarp[lane] = ti - t;
+    if (lane == NW - 1) sWarp[NW] = ti;
+  }
+  __syncthreads();
+  total = sWarp[NW];
+  const int r = sWarp[w] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------- field (§2 step 2)
+// Round-to-nearest-even conversion of a 128-bit integer to double.
+__device__ __forceinline__ double i128_to_f64(__int128 v) {
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  const unsigned __int128 u =
+      neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  if (msb <= 52) {
+    const double d = (double)lo;  // exact
+    return neg ? -d : d;
+  }
+  int sh = msb - 52;
+  unsigned long long mant = (unsigned long long)(u >> sh);  // 53 significant bits
+  const unsigned __int128 rem = u - ((unsigned __int128)mant << sh);
+  const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+  if (rem > half || (rem == half && (mant & 1ull))) {
+    ++mant;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++sh;
+    }
+  }
+  const unsigned long long bits =
+      ((unsigned long long)(sh + 52 + 1023) << 52) | (mant & ((1ull << 52) - 1ull));
+  const double d = __longlong_as_double((long long)bits);
+  return neg ? -d : d;
+}
+
+__device__ __forceinline__ __int128 shfl_up_i128(__int128 v, int o) {
+  unsigned long long lo = (unsigned long long)v;
+  unsigned long long hi = (unsigned long long)((unsigned __int128)v >> 64);
+  lo = __shfl_up_sync(0xffffffffu, lo, o);
+  hi = __shfl_up_sync(0xffffffffu, hi, o);
+  return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+
+// Exclusive block scan of two int128 values (exact: integer sums are order-free).
+__device__ __forceinline__ void block_scan_i128x2(__int128& a, __int128& b, __int128& tb) {
+  __shared__ __int128 wa[33], wb[33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __int128 ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const __int128 ya = shfl_up_i128(ia, o), yb = shfl_up_i128(ib, o);
+    if (lane >= o) {
+      ia += ya;
+      ib += yb;
+    }
+  }
+  if (lane == 31) {
+    wa[w] = ia;
+    wb[w] = ib;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const __int128 xa = (lane < nw) ? wa[lane] : (__int128)0;
+    const __int128 xb = (lane < nw) ? wb[lane] : (__int128)0;
+    __int128 sa = xa, sb = xb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const __int128 ya = shfl_up_i128(sa, o), yb = shfl_up_i128(sb, o);
+      if (lane >= o) {
+        sa += ya;
+        sb += yb;
+      }
+    }
+    if (lane < nw) {
+      wa[lane] = sa - xa;
+      wb[lane] = sb - xb;
+    }
+    if (lane == nw - 1) wb[32] = sb;
+  }
+  __syncthreads();
+  const __int128 ea = wa[w] + ia - a, eb = wb[w] + ib - b;
+  tb = wb[32];
+  __syncthreads();
+  a = ea;
+  b = eb;
+}
+
+// Field of step `step` from the counts of buffer `buf` (reading C-23): the tridiagonal
+// system of §2 step 2 solved through its discrete Green's function,
+//   S_j = (N-j) sum_{k<=j} k dC_k + j sum_{k>j} (N-k) dC_k   (exact int128 prefix sums),
+//   phi_j = (V (N-j) + rfac S_j) / N,
+//   E_j = (2V + rfac (S_{j-1} - S_{j+1})) / (2 N dx)   inside,
+//   E_0 = (V - rfac (S_1 + N dC_0)) / (N dx),  E_N = (V + rfac (S_{N-1} + N dC_N)) / (N dx)
+// (half-cell Gauss law at the electrodes, reading C-4).  Each value rounds once, so the
+// result is independent of the thread count.  Writes the FP64 field, and its FP32 copy in
+// cell units per step squared when K.fE is set.  smem: 16 * nx bytes.
+__device__ __forceinline__ void field_solve(const DevCtx& K, unsigned step, int buf,
+                                            void* smem) {
+  const int N = K.nc, nx = K.nx;
+  __int128* Sg = reinterpret_cast<__int128*>(smem);
+  const unsigned long long* Ce = K.C + (size_t)(buf * 2 + 0) * nx;
+  const unsigned long long* Ci = K.C + (size_t)(buf * 2 + 1) * nx;
+  const double V = K.vtab[step % (unsigned)K.steps_per_rf];  // reading C-2
+  const int seg = (nx + blockDim.x - 1) / blockDim.x;
+  const int j0 = min((int)threadIdx.x * seg, nx), j1 = min(j0 + seg, nx);
+  __int128 sa = 0, sb = 0;
+  for (int j = j0; j < j1; ++j)
+    if (j >= 1 && j <= N - 1) {
+      const long long dc = (long long)Ci[j] - (long long)Ce[j];
+      sa += (__int128)j * dc;
+      sb += (__int128)(N - j) * dc;
+    }
+  __int128 tb;
+  block_scan_i128x2(sa, sb, tb);
+  for (int j = j0; j < j1; ++j) {
+    if (j >= 1 && j <= N - 1) {
+      const long long dc = (long long)Ci[j] - (long long)Ce[j];
+      sa += (__int128)j * dc;
+      sb += (__int128)(N - j) * dc;
+    }
+    Sg[j] = (__int128)(N - j) * sa + (__int128)j * (tb - sb);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+    double e, ph;
+    if (j == 0) {
+      const __int128 q = Sg[1] + (__int128)N * (__int128)((long long)Ci[0] - (long long)Ce[0]);
+      e = __ddiv_rn(__dsub_rn(V, __dmul_rn(K.rfac, i128_to_f64(q))), K.den1);
+      ph = V;
+    } else if (j == N) {
+      const __int128 q =
+          Sg[N - 1] + (__int128)N * (__int128)((long long)Ci[N] - (long long)Ce[N]);
+      e = __ddiv_rn(__dadd_rn(V, __dmul_rn(K.rfac, i128_to_f64(q))), K.den1);
+      ph = 0.0;
+    } else {
+      e = __ddiv_rn(__dadd_rn(__dmul_rn(2.0, V), __dmul_rn(K.rfac, i128_to_f64(Sg[j - 1] - Sg[j + 1]))),
+                    K.den2);
+      ph = __ddiv_rn(__dadd_rn(__dmul_rn(V, (double)(N - j)), __dmul_rn(K.rfac, i128_to_f64(Sg[j]))),
+                     (double)N);
+    }
+    K.E[j] = e;
+    K.phi[j] = ph;
+    if (K.fE[0] != nullptr) {  // FP32 particle state only
+      K.fE[0][j] = (float)__dmul_rn(e, K.fe_scale[0]);
+      K.fE[1][j] = (float)__dmul_rn(e, K.fe_scale[1]);
+    }
+  }
+}
+
+// Block 0 of the placement launch: close step n's accumulation (acc += C(n), counted),
+// clear that buffer for the deposit of step n+1, solve the field of step n+1, advance the
+// step index.
+__device__ __forceinline__ void advance_field(const DevCtx& K, void* smem) {
+  const unsigned m = K.st->step_next;  // n + 1
+  const int done = (m - 1u) & 1u;      // buffer of step n
+  const int nx = K.nx;
+  unsigned long long* Cd = K.C + (size_t)(done * 2) * nx;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+    K.acc[j] += (double)(long long)Cd[j];
+    K.acc[nx + j] += (double)(long long)Cd[nx + j];
+    Cd[j] = 0ull;
+    Cd[nx + j] = 0ull;
+  }
+  field_solve(K, m, m & 1u, smem);
+  if (threadIdx.x == 0) {
+    K.st->steps_avg += 1;
+    K.st->step = m;
+  }
+}
+
+// ------------------------------------------------------------ compaction (reading C-15)
+// The lists of particle block b for a species with n particles start at the slot of the
+// block's first particle (a block lists at most one hole and one birth per particle).
+__device__ __forceinline__ long long list_base(long long n, int b, int G) {
+  return range_begin(n, b, G);
+}
+
+__device__ __forceinline__ int upper_bound_i(const int* a, int n, long long v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((long long)a[mid] <= v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int lower_bound_i(const int* a, int n, long long v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((long long)a[mid] < v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Run by the last particle block to finish (after a fence): exclusive prefixes of the five
+// per-block count arrays in one block scan, the totals of reading C-15 for both species,
+// the new counts and ids.  NW = warps of the block.
+template <int NW>
+__device__ void finalize_compaction(const DevCtx& K, long long ne, long long ni) {
+  constexpr int kA = 5;
+  __shared__ int wsum[NW][kA], wtot[kA];
+  __shared__ long long sq[2];
+  const int G = gridDim.x;
+  int* cnt[kA] = {K.hole_cnt[0], K.hole_cnt[1], K.eb_cnt[0], K.eb_cnt[1], K.ib_cnt};
+  int* pref[kA] = {K.hole_pref[0], K.hole_pref[1], K.eb_pref[0], K.eb_pref[1], K.ib_pref};
+  const int seg = (G + blockDim.x - 1) / blockDim.x;
+  const int c0 = min((int)threadIdx.x * seg, G), c1 = min(c0 + seg, G);
+  int loc[kA];
+#pragma unroll
+  for (int a = 0; a < kA; ++a) {
+    loc[a] = 0;
+    for (int c = c0; c < c1; ++c) loc[a] += cnt[a][c];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc[kA];
+#pragma unroll
+  for (int a = 0; a < kA; ++a) {
+    inc[a] = loc[a];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc[a], o);
+      if (lane >= o) inc[a] += y;
+    }
+    if (lane == 31) wsum[w][a] = inc[a];
+  }
+  __syncthreads();
+  if (threadIdx.x < kA) {  // serial over the few warp sums
+    int run = 0;
+    for (int ww = 0; ww < NW; ++ww) {
+      const int v = wsum[ww][threadIdx.x];
+      wsum[ww][threadIdx.x] = run;
+      run += v;
+    }
+    wtot[threadIdx.x] = run;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < kA; ++a) {
+    // the second electron-birth list continues the ranks of the first
+    int run = wsum[w][a] + inc[a] - loc[a] + (a == 3 ? wtot[2] : 0);
+    for (int c = c0; c < c1; ++c) {
+      pref[a][c] = run;
+      run += cnt[a][c];
+    }
+  }
+  const int He = wtot[0], Hi = wtot[1], Be0 = wtot[2], Be = wtot[2] + wtot[3], Bi = wtot[4];
+  // holes below Nn (needed when tail survivors fill holes): prefix of the block owning Nn
+  // plus its list entries below Nn, counted by the whole block
+  if (threadIdx.x < 2) sq[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const long long N = s ? ni : ne, H = s ? Hi : He, B = s ? Bi : Be;
+    const long long limit = K.cap - (N - H);
+    const long long Beff = B < limit ? B : limit;
+    const long long Nn = N - H + Beff;
+    if (H > Beff) {
+      const int b = range_owner(N, Nn, G);
+      const int* list = K.hole_idx[s] + list_base(N, b, G);
+      const int m = K.hole_cnt[s][b];
+      int below = 0;
+      for (int r = threadIdx.x; r < m; r += blockDim.x) below += ((long long)list[r] < Nn) ? 1 : 0;
+      if (below) atomicAdd((unsigned long long*)&sq[s], (unsigned long long)below);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int s = threadIdx.x;
+    CompactTot t;
+    t.N = s ? ni : ne;
+    t.H = s ? Hi : He;
+    t.B = s ? Bi : Be;
+    t.B0 = s ? Bi : Be0;
+    const long long limit = K.cap - (t.N - t.H);
+    t.Beff = t.B < limit ? t.B : limit;
+    t.Nn = t.N - t.H + t.Beff;
+    t.q = 0;
+    if (t.H > t.Beff) t.q = K.hole_pref[s][range_owner(t.N, t.Nn, G)] + sq[s];
+    t.pad = 0;
+    t.nid = K.st->next_id[s];
+    K.st->tot[s] = t;
+    K.st->n[s] = t.Nn;
+    K.st->next_id[s] = t.nid + (unsigned)t.Beff;
+    if (t.B > t.Beff) {
+      atomicOr(&K.st->status, kStCapacity);
+      atomicAdd(&K.counters[kCnDropped], (unsigned long long)(t.B - t.Beff));
+    }
+  }
+  if (threadIdx.x == 0) K.st->done_blocks = 0u;
+}
+
+// Index of the hole of rank r of species s.
+__device__ __forceinline__ long long hole_of_rank(const DevCtx& K, int s, long long r,
+                                                  const CompactTot& t) {
+  const int b = upper_bound_i(K.hole_pref[s], K.nlist, r) - 1;
+  return K.hole_idx[s][list_base(t.N, b, K.nlist) + (r - K.hole_pref[s][b])];
+}
+
+// Placement launch: block 0 advances the field; the other blocks place every birth (into
+// the holes by rank, then after N) and move every tail survivor (index >= Nn, not a hole)
+// into the remaining holes below Nn, in ascending order.  P supplies the record moves of
+// the particle representation: P::birth(K, s, list, slot, d, id) and P::move(K, s, t, d).
+template <class P>
+__global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
+  extern __shared__ __align__(16) unsigned char place_smem[];
+  if (blockIdx.x == 0) {
+    advance_field(K, place_smem);
+    return;
+  }
+  const CompactTot te = K.st->tot[0], ti = K.st->tot[1];
+  const long long tle = te.H > te.Beff ? te.N - te.Nn : 0;
+  const long long tli = ti.H > ti.Beff ? ti.N - ti.Nn : 0;
+  const long long n_items = te.Beff + tle + ti.Beff + tli;
+  for (long long u = (long long)(blockIdx.x - 1) * blockDim.x + threadIdx.x; u < n_items;
+       u += (long long)(gridDim.x - 1) * blockDim.x) {
+    long long v = u;
+    int s;
+    bool birth;
+    if (v < te.Beff) {
+      s = 0; birth = true;
+    } else if ((v -= te.Beff) < tle) {
+      s = 0; birth = false;
+    } else if ((v -= tle) < ti.Beff) {
+      s = 1; birth = true;
+    } else {
+      v -= ti.Beff;
+      s = 1; birth = false;
+    }
+    const CompactTot& t = s ? ti : te;
+    if (birth) {
+      const long long r = v;
+      int list, b;
+      long long slot;
+      // electron births come from the blocks' electron ranges (ionization) and ion ranges
+      // (emission); ion births from the electron ranges
+      if (s == 0 && r < t.B0) {
+        list = 0;
+        b = upper_bound_i(K.eb_pref[0], K.nlist, r) - 1;
+        slot = list_base(te.N, b, K.nlist) + (r - K.eb_pref[0][b]);
+      } else if (s == 0) {
+        list = 1;
+        b = upper_bound_i(K.eb_pref[1], K.nlist, r) - 1;
+        slot = list_base(ti.N, b, K.nlist) + (r - K.eb_pref[1][b]);
+      } else {
+        list = 2;
+        b = upper_bound_i(K.ib_pref, K.nlist, r) - 1;
+        slot = list_base(te.N, b, K.nlist) + (r - K.ib_pref[b]);
+      }
+      const long long d = (r < t.H) ? hole_of_rank(K, s, r, t) : t.N + r - t.H;
+      P::birth(K, s, list, slot, d, t.nid + (unsigned)r);
+    } else {
+      const long long idx = t.Nn + v;  // a tail position
+      const int b = range_owner(t.N, idx, K.nlist);
+      const int* list = K.hole_idx[s] + list_base(t.N, b, K.nlist);
+      const int m = K.hole_cnt[s][b];
+      const int lb = lower_bound_i(list, m, idx);
+      if (lb < m && list[lb] == idx) continue;  // the tail position is itself a hole
+      const long long before = (long long)K.hole_pref[s][b] + lb;  // holes below idx
+      const long long j = (idx - t.Nn) - (before - t.q);             // rank among survivors
+      P::move(K, s, idx, hole_of_rank(K, s, t.Beff + j, t));
+    }
+  }
+}
+
+}  // namespace pic

@@ -26,6 +26,42 @@ enum : int {
   kCnIIso, kCnICx, kCnECand, kCnICand, kCnEepfN, kCnEepfEsum, kCnDropped
 };
 
+// Compaction totals of one species for the current step (written by the last particle
+// block, read by the placement launch).
+struct CompactTot {
+  long long N;     // particles before the step
+  long long H;     // holes (removed particles)
+  long long B;     // births (all sources)
+  long long B0;    // births of the first source (electrons: ionization; ions: all)
+  long long Beff;  // births that fit the capacity
+  long long Nn;    // particles after the step
+  long long q;     // holes below Nn
+  unsigned nid;    // id of the first birth
+  int pad;
+};
+
+// Particle block b of a grid of G blocks owns the particles [range_begin(b), range_begin(b+1))
+// of each species: contiguous, balanced to one 32-particle unit, starting on an even index.
+constexpr int kUnit = 32;
+__host__ __device__ __forceinline__ long long range_begin(long long n, int b, int G) {
+  const long long units = (n + kUnit - 1) / kUnit;
+  const long long u = (units * (long long)b) / G;
+  const long long p = u * kUnit;
+  return p < n ? p : n;
+}
+// The block whose range holds particle index t (0 <= t < n).
+__host__ __device__ __forceinline__ int range_owner(long long n, long long t, int G) {
+  const long long units = (n + kUnit - 1) / kUnit;
+  const long long u = t / kUnit;
+  // smallest b with range_begin(b+1) > t, i.e. floor(units (b+1) / G) > u
+  long long b = ((u + 1) * (long long)G + units - 1) / units - 1;
+  if (b < 0) b = 0;
+  if (b > G - 1) b = G - 1;
+  while (b > 0 && range_begin(n, (int)b, G) > t) --b;
+  while (b < G - 1 && range_begin(n, (int)b + 1, G) <= t) ++b;
+  return (int)b;
+}
+
 // Device-resident scalars that change every step.
 struct DevState {
   long long n[2];       // live particles per species
@@ -36,6 +72,9 @@ struct DevState {
   int status;           // sticky kSt* bits
   long long steps_avg;  // steps added to the RF-average accumulators
   unsigned long long vmax_bits;  // scratch of the |vx| maximum reduction
+  unsigned done_blocks;          // particle blocks finished in the current pass
+  unsigned pad;
+  CompactTot tot[2];
 };
 
 // Everything a kernel needs, passed by value (constant bank).  Pointers address the
@@ -57,17 +96,21 @@ struct DevCtx {
   // grid: counts C[buf][species][nx], potential, field, density accumulators [2][nx]
   unsigned long long *C;
   double *phi, *E, *acc;
+  float* fE[2];        // FP32 path: per-species velocity kick per step in cells/step (or null)
+  double fe_scale[2];  // E [V/m] -> kick: (q/m) dt^2 / dx
   const double *inv_den, *vtab, *F[2];
   unsigned long long *eepf, *fedf, *counters;  // fedf [2][fedf_bins]
   DevState *st;
-  // per-step scratch (hole / birth bookkeeping)
-  int *hole_idx[2];     // [cap]: holes of chunk c at c*kChunk + rank
-  int *hole_cnt[2];     // [nchunk_max]
-  int *eb_cnt[2];       // electron births per chunk of species s
-  int *ib_cnt;          // ion births per electron chunk
-  double *eb[2];        // [4][cap] records x, vx, vy, vz of electron births from species s
-  double *ib;           // [4][cap] ion births from electron chunks
-  int *hole_sorted[2];  // [cap] all holes of a species in ascending order
+  // per-step scratch (hole / birth bookkeeping).  Particle block b owns a contiguous range
+  // of chunks; its lists start at the slot of its first chunk of each species and are in
+  // particle order.  Counts and exclusive prefixes are per block ([nlist] entries).
+  int nlist;            // entries of the per-block count arrays (>= the particle grid)
+  int *hole_idx[2];     // [cap]: hole indices
+  int *hole_cnt[2], *hole_pref[2];
+  int *eb_cnt[2], *eb_pref[2];  // electron births from blocks' species-s chunks
+  int *ib_cnt, *ib_pref;        // ion births from blocks' electron chunks
+  double *eb[2];        // [4][cap] records x, vx, vy, vz of electron births (FP64 state)
+  double *ib;           // [4][cap] ion births (FP64 state)
 };
 
 // ------------------------------------------------------------------ Philox4x32-10

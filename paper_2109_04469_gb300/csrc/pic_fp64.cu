@@ -4,16 +4,18 @@
 // reproduce the FP64 CPU oracle bit for bit on identical inputs and random keys.
 //
 // Step n is two launches:
-//   k_push_fp64(n)     steps 3-6 of §2 and the deposit (step 1) of x^{n+1}: one pass over
-//                      the particle state, persistent grid, block-private smem grids;
-//   k_compact_field(n) blocks 0/1 remove absorbed particles and insert births (one block per
-//                      species); block 2 closes step n's RF-average accumulation and solves
-//                      steps 1-2 (counts -> rho -> phi -> E) for step n+1, which depend only
-//                      on the deposit, so the field solve overlaps the compaction.
+//   k_push_fp64(n)   steps 3-6 of §2 and the deposit (step 1) of x^{n+1}: one pass over the
+//                    particle state, persistent grid, block-private smem grids; each block
+//                    owns a contiguous range of chunks and lists its holes and births in
+//                    particle order; the last block to finish totals the lists;
+//   k_place_field(n) places births and tail survivors (reading C-15) in parallel, while
+//                    block 0 closes step n's RF average and solves the field of step n+1
+//                    (§2 steps 1-2), which depends only on the deposit.
 // The counts, the step index and the particle numbers live on the device: no step needs
 // the host.
 #include <cuda_runtime.h>
 
+#include "pic_common.cuh"
 #include "pic_dev.cuh"
 #include "pic_launch.h"
 
@@ -69,35 +71,6 @@ __device__ __forceinline__ void lookup(const double* __restrict__ F, double eps,
   f2 = a23.x + fr * (b23.x - a23.x);
 }
 
-template <int NW>
-__device__ __forceinline__ int block_excl_scan(int v, int* sWarp, int& total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) sWarp[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    const int t = (lane < NW) ? sWarp[lane] : 0;
-    int ti = t;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, ti, o);
-      if (lane >= o) ti += y;
-    }
-    if (lane < NW) sWarp[lane] = ti - t;
-    if (lane == NW - 1) sWarp[NW] = ti;
-  }
-  __syncthreads();
-  total = sWarp[NW];
-  const int r = sWarp[w] + inc - v;
-  __syncthreads();
-  return r;
-}
-
 // ------------------------------------------------------------------ initial load
 // Reading C-22: uniform x in (0, L), Maxwellian velocities, ids 0..n0-1, streams at step
 // 0xFFFFFFFF.
@@ -147,147 +120,7 @@ __global__ void k_max_abs(const double* __restrict__ v, long long n, unsigned lo
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
-// ------------------------------------------------------------------- field (§2 step 2)
-// Round-to-nearest-even conversion of a 128-bit integer to double (the one rounding of each
-// field value).
-__device__ __forceinline__ double i128_to_f64(__int128 v) {
-  if (v == 0) return 0.0;
-  const bool neg = v < 0;
-  const unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
-  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-  if (msb <= 52) {
-    const double d = (double)lo;  // exact
-    return neg ? -d : d;
-  }
-  int sh = msb - 52;
-  unsigned long long mant = (unsigned long long)(u >> sh);  // 53 significant bits
-  const unsigned __int128 rem = u - ((unsigned __int128)mant << sh);
-  const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-  if (rem > half || (rem == half && (mant & 1ull))) {
-    ++mant;
-    if (mant == (1ull << 53)) {
-      mant >>= 1;
-      ++sh;
-    }
-  }
-  const unsigned long long bits =
-      ((unsigned long long)(sh + 52 + 1023) << 52) | (mant & ((1ull << 52) - 1ull));
-  const double d = __longlong_as_double((long long)bits);
-  return neg ? -d : d;
-}
-
-__device__ __forceinline__ __int128 shfl_up_i128(__int128 v, int o) {
-  unsigned long long lo = (unsigned long long)v;
-  unsigned long long hi = (unsigned long long)((unsigned __int128)v >> 64);
-  lo = __shfl_up_sync(0xffffffffu, lo, o);
-  hi = __shfl_up_sync(0xffffffffu, hi, o);
-  return (__int128)(((unsigned __int128)hi << 64) | lo);
-}
-
-// Exclusive block scan of two int128 values (exact: integer sums are order-free).
-__device__ __forceinline__ void block_scan_i128x2(__int128& a, __int128& b, __int128& ta,
-                                                  __int128& tb) {
-  __shared__ __int128 wa[33], wb[33];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  __int128 ia = a, ib = b;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const __int128 ya = shfl_up_i128(ia, o), yb = shfl_up_i128(ib, o);
-    if (lane >= o) {
-      ia += ya;
-      ib += yb;
-    }
-  }
-  if (lane == 31) {
-    wa[w] = ia;
-    wb[w] = ib;
-  }
-  __syncthreads();
-  if (w == 0) {
-    __int128 xa = (lane < nw) ? wa[lane] : (__int128)0, xb = (lane < nw) ? wb[lane] : (__int128)0;
-    __int128 sa = xa, sb = xb;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const __int128 ya = shfl_up_i128(sa, o), yb = shfl_up_i128(sb, o);
-      if (lane >= o) {
-        sa += ya;
-        sb += yb;
-      }
-    }
-    if (lane < nw) {
-      wa[lane] = sa - xa;
-      wb[lane] = sb - xb;
-    }
-    if (lane == nw - 1) {
-      wa[32] = sa;
-      wb[32] = sb;
-    }
-  }
-  __syncthreads();
-  const __int128 ea = wa[w] + ia - a, eb = wb[w] + ib - b;
-  ta = wa[32];
-  tb = wb[32];
-  __syncthreads();
-  a = ea;
-  b = eb;
-}
-
-// Field of step `step` from the counts of buffer `buf` (reading C-23): the tridiagonal
-// system of §2 step 2 solved through its discrete Green's function,
-//   S_j = (N-j) sum_{k<=j} k dC_k + j sum_{k>j} (N-k) dC_k   (exact int128 prefix sums),
-//   phi_j = (V (N-j) + rfac S_j) / N,
-//   E_j = (2V + rfac (S_{j-1} - S_{j+1})) / (2 N dx)   inside,
-//   E_0 = (V - rfac (S_1 + N dC_0)) / (N dx),  E_N = (V + rfac (S_{N-1} + N dC_N)) / (N dx)
-// (half-cell Gauss law at the electrodes, reading C-4).  Each value rounds once, so the
-// result is independent of the thread count.  smem: 16 * nx bytes.
-__device__ __forceinline__ void field_solve(const DevCtx& K, unsigned step, int buf,
-                                            void* smem) {
-  const int N = K.nc, nx = K.nx;
-  __int128* Sg = reinterpret_cast<__int128*>(smem);
-  const unsigned long long* Ce = K.C + (size_t)(buf * 2 + 0) * nx;
-  const unsigned long long* Ci = K.C + (size_t)(buf * 2 + 1) * nx;
-  const double V = K.vtab[step % (unsigned)K.steps_per_rf];  // reading C-2
-  const int seg = (nx + blockDim.x - 1) / blockDim.x;
-  const int j0 = min((int)threadIdx.x * seg, nx), j1 = min(j0 + seg, nx);
-  __int128 sa = 0, sb = 0;
-  for (int j = j0; j < j1; ++j)
-    if (j >= 1 && j <= N - 1) {
-      const long long dc = (long long)Ci[j] - (long long)Ce[j];
-      sa += (__int128)j * dc;
-      sb += (__int128)(N - j) * dc;
-    }
-  __int128 ta, tb;
-  block_scan_i128x2(sa, sb, ta, tb);
-  for (int j = j0; j < j1; ++j) {
-    if (j >= 1 && j <= N - 1) {
-      const long long dc = (long long)Ci[j] - (long long)Ce[j];
-      sa += (__int128)j * dc;
-      sb += (__int128)(N - j) * dc;
-    }
-    Sg[j] = (__int128)(N - j) * sa + (__int128)j * (tb - sb);
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-    double e, ph;
-    if (j == 0) {
-      const __int128 q = Sg[1] + (__int128)N * (__int128)((long long)Ci[0] - (long long)Ce[0]);
-      e = (V - K.rfac * i128_to_f64(q)) / K.den1;
-      ph = V;
-    } else if (j == N) {
-      const __int128 q = Sg[N - 1] + (__int128)N * (__int128)((long long)Ci[N] - (long long)Ce[N]);
-      e = (V + K.rfac * i128_to_f64(q)) / K.den1;
-      ph = 0.0;
-    } else {
-      e = (2.0 * V + K.rfac * i128_to_f64(Sg[j - 1] - Sg[j + 1])) / K.den2;
-      ph = (V * (double)(N - j) + K.rfac * i128_to_f64(Sg[j])) / (double)N;
-    }
-    K.E[j] = e;
-    K.phi[j] = ph;
-  }
-}
-
-// Stand-alone solve for the current step (after init, set_particles, set_step, or on
+// Stand-alone field solve for the current step (after init, set_particles, set_step, or on
 // request); touches no accumulator.
 __global__ void k_field(DevCtx K) {
   extern __shared__ __align__(16) unsigned char fsm[];
@@ -486,23 +319,23 @@ __device__ __forceinline__ bool step_particle(const DevCtx& K, unsigned step, lo
   return false;
 }
 
-// One chunk of kChunk particles of species S: two 512-particle passes; each thread moves a
-// pair of neighbours with 128-bit loads/stores.  Holes and births are ranked in particle
-// order with a block scan and written to the chunk's slots of the scratch lists.
+// The block's particles [pb, pe) of species S (pb even), in 512-particle passes; each thread
+// moves a pair of neighbours with 128-bit loads/stores.  Holes and births are ranked in
+// particle order with a block scan and appended to the block's lists (which start at pb).
 template <int S>
-__device__ __forceinline__ void chunk_pass(const DevCtx& K, unsigned step, int c, long long n,
-                                           const double* sE, unsigned long long* sCe,
-                                           unsigned long long* sCi, unsigned long long* sCnt,
-                                           int* sWarp, int* sRun) {
-  const long long cbase = (long long)c * kChunk;
+__device__ __forceinline__ void range_pass(const DevCtx& K, unsigned step, long long pb,
+                                           long long pe, const double* sE,
+                                           unsigned long long* sCe, unsigned long long* sCi,
+                                           unsigned long long* sCnt, int* sWarp, int* sRun) {
   const size_t cap = (size_t)K.nchunk_max * kChunk;
-  for (int t = 0; t < kChunk / kTile; ++t) {
-    const long long p0 = cbase + (long long)t * kTile + 2 * threadIdx.x;
+  const long long lbase = pb;
+  for (long long tile = pb; tile < pe; tile += kTile) {
+    const long long p0 = tile + 2 * threadIdx.x;
     bool dead0 = false, dead1 = false;
     Births b0, b1;
     b0.e = b0.i = b1.e = b1.i = false;
-    if (p0 < n) {
-      const bool both = (p0 + 1 < n);
+    if (p0 < pe) {
+      const bool both = (p0 + 1 < pe);
       double x0, x1 = 0.0, v0, v1 = 0.0;
       unsigned id0, id1 = 0;
       if (both) {
@@ -530,26 +363,26 @@ __device__ __forceinline__ void chunk_pass(const DevCtx& K, unsigned step, int c
     const int i = (int)b0.i + (int)b1.i;
     int total;
     const int ex = block_excl_scan<kBlock / 32>(h | (e << 10) | (i << 20), sWarp, total);
-    int hk = sRun[0] + (ex & 1023);
-    int ek = sRun[1] + ((ex >> 10) & 1023);
-    int ik = sRun[2] + ((ex >> 20) & 1023);
-    if (dead0) K.hole_idx[S][cbase + hk++] = (int)p0;
-    if (dead1) K.hole_idx[S][cbase + hk++] = (int)(p0 + 1);
+    long long hk = lbase + sRun[0] + (ex & 1023);
+    long long ek = lbase + sRun[1] + ((ex >> 10) & 1023);
+    long long ik = lbase + sRun[2] + ((ex >> 20) & 1023);
+    if (dead0) K.hole_idx[S][hk++] = (int)p0;
+    if (dead1) K.hole_idx[S][hk++] = (int)(p0 + 1);
     if (b0.e) {
-      double* E4 = K.eb[S] + cbase + ek++;
+      double* E4 = K.eb[S] + ek++;
       E4[0] = b0.e4[0]; E4[cap] = b0.e4[1]; E4[2 * cap] = b0.e4[2]; E4[3 * cap] = b0.e4[3];
     }
     if (b1.e) {
-      double* E4 = K.eb[S] + cbase + ek++;
+      double* E4 = K.eb[S] + ek++;
       E4[0] = b1.e4[0]; E4[cap] = b1.e4[1]; E4[2 * cap] = b1.e4[2]; E4[3 * cap] = b1.e4[3];
     }
     if (S == 0) {
       if (b0.i) {
-        double* I4 = K.ib + cbase + ik++;
+        double* I4 = K.ib + ik++;
         I4[0] = b0.i4[0]; I4[cap] = b0.i4[1]; I4[2 * cap] = b0.i4[2]; I4[3 * cap] = b0.i4[3];
       }
       if (b1.i) {
-        double* I4 = K.ib + cbase + ik++;
+        double* I4 = K.ib + ik++;
         I4[0] = b1.i4[0]; I4[cap] = b1.i4[1]; I4[2 * cap] = b1.i4[2]; I4[3 * cap] = b1.i4[3];
       }
     }
@@ -560,18 +393,11 @@ __device__ __forceinline__ void chunk_pass(const DevCtx& K, unsigned step, int c
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    K.hole_cnt[S][c] = sRun[0];
-    K.eb_cnt[S][c] = sRun[1];
-    if (S == 0) K.ib_cnt[c] = sRun[2];
-    sRun[0] = sRun[1] = sRun[2] = 0;
-  }
-  __syncthreads();
 }
 
-// Persistent grid over the electron chunks followed by the ion chunks.  Block-private
-// shared-memory copies of E and of the two count grids; the counts are flushed to the
-// global int64 grid with one atomic per touched node at the end.
+// Persistent grid: block b takes its balanced contiguous range of the electrons, then of the
+// ions.  Block-private shared-memory copies of E and of the two count grids, flushed to the
+// global int64 grid with one atomic per touched node.
 __global__ void __launch_bounds__(kBlock, 2) k_push_fp64(DevCtx K) {
   extern __shared__ double psm[];
   const int nx = K.nx;
@@ -580,25 +406,30 @@ __global__ void __launch_bounds__(kBlock, 2) k_push_fp64(DevCtx K) {
   unsigned long long* sCnt = sC + 2 * nx;
   __shared__ int sWarp[kBlock / 32 + 1];
   __shared__ int sRun[3];
+  __shared__ bool sLast;
   for (int j = threadIdx.x; j < nx; j += blockDim.x) sE[j] = K.E[j];
   for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0ull;
   if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) sRun[0] = sRun[1] = sRun[2] = 0;
   const unsigned step = K.st->step;
   const long long ne = K.st->n[0], ni = K.st->n[1];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {  // counts and step the compaction works from
-    K.st->n_snap[0] = ne;
-    K.st->n_snap[1] = ni;
-    K.st->step_next = step + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) K.st->step_next = step + 1;
+  __syncthreads();
+  const int G = gridDim.x, b = blockIdx.x;
+  range_pass<0>(K, step, range_begin(ne, b, G), range_begin(ne, b + 1, G), sE, sC, sC + nx,
+                sCnt, sWarp, sRun);
+  if (threadIdx.x == 0) {
+    K.hole_cnt[0][blockIdx.x] = sRun[0];
+    K.eb_cnt[0][blockIdx.x] = sRun[1];
+    K.ib_cnt[blockIdx.x] = sRun[2];
+    sRun[0] = sRun[1] = sRun[2] = 0;
   }
   __syncthreads();
-  const int nche = (int)((ne + kChunk - 1) / kChunk);
-  const int nchi = (int)((ni + kChunk - 1) / kChunk);
-  for (int vc = blockIdx.x; vc < nche + nchi; vc += gridDim.x) {
-    if (vc < nche)
-      chunk_pass<0>(K, step, vc, ne, sE, sC, sC + nx, sCnt, sWarp, sRun);
-    else
-      chunk_pass<1>(K, step, vc - nche, ni, sE, sC, sC + nx, sCnt, sWarp, sRun);
+  range_pass<1>(K, step, range_begin(ni, b, G), range_begin(ni, b + 1, G), sE, sC, sC + nx,
+                sCnt, sWarp, sRun);
+  if (threadIdx.x == 0) {
+    K.hole_cnt[1][blockIdx.x] = sRun[0];
+    K.eb_cnt[1][blockIdx.x] = sRun[1];
   }
   __syncthreads();
   unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
@@ -608,157 +439,36 @@ __global__ void __launch_bounds__(kBlock, 2) k_push_fp64(DevCtx K) {
   }
   if (threadIdx.x < kNumCounters && sCnt[threadIdx.x])
     atomicAdd(&K.counters[threadIdx.x], sCnt[threadIdx.x]);
-}
-
-// ------------------------------------------------------- compaction (C-15) + next field
-constexpr int kCompactThreads = 1024;
-
-// For every chunk c < nch with cnt[c] entries at chunk-local slots, visit the entries in
-// chunk order with their global rank: f(rank, slot).
-template <typename Fn>
-__device__ __forceinline__ int for_ranked(const int* cnt, int nch, int* sPref, int* sCnt,
-                                          int* sWarp, int rank0, Fn f) {
-  int carry = rank0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int b0 = 0; b0 < nch; b0 += kCompactThreads) {
-    const int c = b0 + threadIdx.x;
-    const int v = (c < nch) ? cnt[c] : 0;
-    int total;
-    const int ex = block_excl_scan<kCompactThreads / 32>(v, sWarp, total);
-    sPref[threadIdx.x] = ex;
-    sCnt[threadIdx.x] = v;
-    __syncthreads();
-    const int nb = min(kCompactThreads, nch - b0);
-    for (int cc = warp; cc < nb; cc += kCompactThreads / 32) {
-      const int m = sCnt[cc];
-      const int base = carry + sPref[cc];
-      const long long slot0 = (long long)(b0 + cc) * kChunk;
-      for (int r = lane; r < m; r += 32) f(base + r, slot0 + r);
-    }
-    carry += total;
-    __syncthreads();
-  }
-  return carry;
-}
-
-__device__ void compact_species(const DevCtx& K, int s, int* sPref, int* sCnt, int* sWarp) {
-  const long long N = K.st->n_snap[s];
-  const long long Ne = K.st->n_snap[0], Ni = K.st->n_snap[1];
-  const int nch = (int)((N + kChunk - 1) / kChunk);
-  const int nche = (int)((Ne + kChunk - 1) / kChunk), nchi = (int)((Ni + kChunk - 1) / kChunk);
-  const size_t cap = (size_t)K.nchunk_max * kChunk;
-  int* hs = K.hole_sorted[s];
-  const int* hidx = K.hole_idx[s];
-  // 1. all holes in ascending order
-  const int H = for_ranked(K.hole_cnt[s], nch, sPref, sCnt, sWarp, 0,
-                           [&](int rank, long long slot) { hs[rank] = hidx[slot]; });
+  // the last block to finish totals the lists (no block waits for another)
+  __threadfence();
+  if (threadIdx.x == 0) sLast = (atomicAdd(&K.st->done_blocks, 1u) == gridDim.x - 1);
   __syncthreads();
-  // 2. births in rank order: into the holes, then appended after N
-  const long long limit = K.cap - (N - H);
-  const unsigned nid = K.st->next_id[s];
-  double* X = K.x[s];
-  double* VX = K.vx[s];
-  double* VY = K.vy[s];
-  double* VZ = K.vz[s];
-  unsigned* ID = K.id[s];
-  auto place = [&](const double* rec) {
-    return [=](int rank, long long slot) {
-      if (rank >= limit) return;
-      const long long d = (rank < H) ? (long long)hs[rank] : N + rank - H;
-      X[d] = rec[slot];
-      VX[d] = rec[slot + cap];
-      VY[d] = rec[slot + 2 * cap];
-      VZ[d] = rec[slot + 3 * cap];
-      ID[d] = nid + (unsigned)rank;
-    };
-  };
-  int B;
-  if (s == 0) {
-    B = for_ranked(K.eb_cnt[0], nche, sPref, sCnt, sWarp, 0, place(K.eb[0]));
-    B = for_ranked(K.eb_cnt[1], nchi, sPref, sCnt, sWarp, B, place(K.eb[1]));
-  } else {
-    B = for_ranked(K.ib_cnt, nche, sPref, sCnt, sWarp, 0, place(K.ib));
-  }
-  const long long Beff = (B < limit) ? (long long)B : limit;
-  const long long Nn = N - H + Beff;
-  // 3. tail survivors (indices >= Nn that are not holes) fill the remaining holes below Nn
-  //    in ascending order.  The holes at or above Nn are the sorted suffix hs[q..H); each
-  //    1024-index tile of the tail marks its holes in shared memory.
-  if (H > Beff) {
-    int* sFlag = sCnt;
-    int q = 0;
-    {  // first hole index >= Nn: count of holes below Nn, by a block reduction
-      int below = 0;
-      for (int r = threadIdx.x; r < H; r += kCompactThreads) below += (hs[r] < Nn) ? 1 : 0;
-      int total;
-      (void)block_excl_scan<kCompactThreads / 32>(below, sWarp, total);
-      q = total;
-    }
-    int carry = 0, hq = q;
-    for (long long b0 = Nn; b0 < N; b0 += kCompactThreads) {
-      sFlag[threadIdx.x] = 0;
-      __syncthreads();
-      // holes in [b0, b0 + 1024) are hs[hq .. hq + m): at most 1024 of them
-      const int r = hq + threadIdx.x;
-      const bool inr = r < H && (long long)hs[r] < b0 + kCompactThreads;
-      if (inr) sFlag[hs[r] - b0] = 1;
-      int m;
-      (void)block_excl_scan<kCompactThreads / 32>((int)inr, sWarp, m);
-      const long long idx = b0 + threadIdx.x;
-      const bool surv = idx < N && !sFlag[threadIdx.x];
-      int total;
-      const int ex = block_excl_scan<kCompactThreads / 32>((int)surv, sWarp, total);
-      if (surv) {
-        const long long d = hs[Beff + carry + ex];
-        X[d] = X[idx];
-        VX[d] = VX[idx];
-        VY[d] = VY[idx];
-        VZ[d] = VZ[idx];
-        ID[d] = ID[idx];
-      }
-      carry += total;
-      hq += m;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    K.st->n[s] = Nn;
-    K.st->next_id[s] = nid + (unsigned)Beff;
-    if (B > Beff) {
-      atomicOr(&K.st->status, kStCapacity);
-      atomicAdd(&K.counters[kCnDropped], (unsigned long long)(B - Beff));
-    }
+  if (sLast) {
+    __threadfence();
+    finalize_compaction<kBlock / 32>(K, ne, ni);
   }
 }
 
-// Block 2: close step n's accumulation (acc += C(n), counted) and clear that buffer for the
-// deposit of step n+1, then solve the field of step n+1.
-__device__ void advance_field(const DevCtx& K, void* smem) {
-  const unsigned m = K.st->step_next;  // n + 1
-  const int done = (m - 1u) & 1u;      // buffer of step n
-  const int nx = K.nx;
-  unsigned long long* Cd = K.C + (size_t)(done * 2) * nx;
-  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-    K.acc[j] += (double)(long long)Cd[j];
-    K.acc[nx + j] += (double)(long long)Cd[nx + j];
-    Cd[j] = 0ull;
-    Cd[nx + j] = 0ull;
+// Record moves of the FP64 representation for the placement launch.
+struct Fp64Moves {
+  static __device__ __forceinline__ void birth(const DevCtx& K, int s, int list, long long slot,
+                                               long long d, unsigned id) {
+    const double* rec = list == 0 ? K.eb[0] : (list == 1 ? K.eb[1] : K.ib);
+    const size_t cap = (size_t)K.nchunk_max * kChunk;
+    K.x[s][d] = rec[slot];
+    K.vx[s][d] = rec[slot + cap];
+    K.vy[s][d] = rec[slot + 2 * cap];
+    K.vz[s][d] = rec[slot + 3 * cap];
+    K.id[s][d] = id;
   }
-  if (threadIdx.x == 0) K.st->steps_avg += 1;
-  field_solve(K, m, m & 1u, smem);
-}
-
-__global__ void __launch_bounds__(kCompactThreads) k_compact_field(DevCtx K) {
-  extern __shared__ __align__(16) unsigned char csm[];
-  __shared__ int sPref[kCompactThreads], sCnt[kCompactThreads];
-  __shared__ int sWarp[kCompactThreads / 32 + 1];
-  if (blockIdx.x < 2) {
-    compact_species(K, blockIdx.x, sPref, sCnt, sWarp);
-    if (blockIdx.x == 0 && threadIdx.x == 0) K.st->step = K.st->step_next;
-  } else {
-    advance_field(K, csm);
+  static __device__ __forceinline__ void move(const DevCtx& K, int s, long long t, long long d) {
+    K.x[s][d] = K.x[s][t];
+    K.vx[s][d] = K.vx[s][t];
+    K.vy[s][d] = K.vy[s][t];
+    K.vz[s][d] = K.vz[s][t];
+    K.id[s][d] = K.id[s][t];
   }
-}
+};
 
 // ------------------------------------------------------------------------ launchers
 size_t field_smem_bytes(int nx) { return sizeof(__int128) * (size_t)nx; }
@@ -790,8 +500,8 @@ cudaError_t launch_push_fp64(const DevCtx& K, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact_field(const DevCtx& K, cudaStream_t s) {
-  k_compact_field<<<3, kCompactThreads, field_smem_bytes(K.nx), s>>>(K);
+cudaError_t launch_place_fp64(const DevCtx& K, int grid, cudaStream_t s) {
+  k_place_field<Fp64Moves><<<grid, 256, field_smem_bytes(K.nx), s>>>(K);
   return cudaGetLastError();
 }
 
@@ -813,8 +523,8 @@ cudaError_t configure_kernels(int nx) {
   cudaError_t e = cudaFuncSetAttribute(k_push_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)push_smem_bytes(nx));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_compact_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)field_smem_bytes(nx));
+  e = cudaFuncSetAttribute(k_place_field<Fp64Moves>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem_bytes(nx));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)field_smem_bytes(nx));

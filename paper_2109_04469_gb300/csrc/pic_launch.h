@@ -15,8 +15,9 @@ cudaError_t launch_deposit(const DevCtx& K, int species, int buf, long long n, c
 cudaError_t launch_field(const DevCtx& K, cudaStream_t s);
 // particle pass of the current step
 cudaError_t launch_push_fp64(const DevCtx& K, int grid, cudaStream_t s);
-// compaction of the current step, accumulation, field of the next step, step += 1
-cudaError_t launch_compact_field(const DevCtx& K, cudaStream_t s);
+// placement of births and tail survivors of the current step; block 0 closes the step's
+// accumulation, solves the field of the next step and advances the step index
+cudaError_t launch_place_fp64(const DevCtx& K, int grid, cudaStream_t s);
 cudaError_t launch_set_step(const DevCtx& K, unsigned step, cudaStream_t s);
 cudaError_t launch_max_abs(const double* v, long long n, unsigned long long* out,
                            cudaStream_t s);
