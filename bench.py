@@ -35,7 +35,8 @@ UNIT = "particle-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 PROFILE_DIR = os.path.join(ROOT, "profiles")
-PUSH_SOURCES = ("paper_2109_04469_gb300/csrc/pic_fp64.cu", "paper_2109_04469_gb300/csrc/pic_dev.cuh")
+PUSH_SOURCES = ("paper_2109_04469_gb300/csrc/pic_fp64.cu", "paper_2109_04469_gb300/csrc/pic_dev.cuh",
+                "paper_2109_04469_gb300/csrc/pic_common.cuh")
 
 
 def parse():
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--precisions", default="fp32,fp64",
+                    help="comma list; the first is the headline, the others are reported beside it")
     return ap.parse_args()
 
 
@@ -83,7 +86,8 @@ def profiled_traffic(kernel: str, workload: str):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("source_sha256_16") != source_hash(PUSH_SOURCES):
+    srcs = tuple(s.strip() for s in vals.get("sources", ",".join(PUSH_SOURCES)).split(","))
+    if vals.get("source_sha256_16") != source_hash(srcs):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full_workload"])
@@ -197,6 +201,96 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+BYTES_PER_PARTICLE = {  # algorithmic bytes of the particle pass per particle-step
+    # FP64: x, vx read and written (32 B) + id read (4 B); a candidate also reads and writes
+    # vy, vz (32 B); a removed or born particle moves one 36 B record
+    "fp64": (36.0, 32.0, 36.0),
+    # FP32: offset, vx read and written (16 B) + 16-bit cell and countdown read and written
+    # (8 B) + id read
+    # (4 B); candidates r/w vy, vz (16 B); a moved record is 24 B
+    "fp32": (28.0, 16.0, 24.0),
+}
+
+
+def measure(pcfg: dict, precision: str, args, torch, dist, local_rank: int,
+            with_e2e: bool) -> dict:
+    """Time args.steps steps of one precision (CUDA events on the library's stream, L2
+    flushed between steps, clocks sampled during the timed region)."""
+    from paper_2109_04469_gb300 import pic
+
+    cfg = dict(pcfg)
+    cfg["precision"] = pic.PIC_FP32 if precision == "fp32" else pic.PIC_FP64
+    sim = pic.Simulation(cfg)
+    stream = sim.stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    sim.step(args.warmup)
+    sim.sync()
+    c0 = sim.accum()["counters"].astype(np.int64)
+    try:
+        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms = 0.0
+    parts = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k)  # L2 flush between timed steps (outside the events)
+            ne, ni = sim.counts()
+            parts += ne + ni
+            ev0.record(stream)
+            sim.step(1)  # the step's two launches, nothing else between the events
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms += ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    dc = sim.accum()["counters"].astype(np.int64) - c0  # events of the timed steps
+    # per-launch split from a second pass with events around each launch
+    ms2 = np.zeros(2)  # particle pass, placement (+ next field solve beside it)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k)
+            sim.step_profiled(1, ms2)
+    field_ms = 0.0  # the field solve on its own (it runs beside the placement in a step)
+    with torch.cuda.stream(stream):
+        for k in range(10):
+            ev0.record(stream)
+            sim.solve_field()
+            ev1.record(stream)
+            ev1.synchronize()
+            field_ms += ev0.elapsed_time(ev1) / 10
+    status = sim.status()
+    per, cand, rec = BYTES_PER_PARTICLE[precision]
+    turnover = int(dc[0] + dc[1] + dc[2] + dc[3] + 2 * dc[8] + dc[5])
+    alg_bytes = per * parts + cand * float(dc[11] + dc[12]) + rec * turnover
+    out = dict(step_ms=step_ms, parts=parts, push_ms=ms2[0] / args.steps,
+               place_ms=ms2[1] / args.steps, field_ms=field_ms,
+               alg_bytes_per_launch=alg_bytes / args.steps, clocks=clocks, status=status)
+    if with_e2e:
+        out["e2e"] = run_e2e(sim, args, torch)
+    sim.close()
+    return out
+
+
+def reduce_ranks(torch, dist, step_ms: float, parts: int):
+    if not dist:
+        return step_ms, parts
+    t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(parts)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(p.item())
+
+
 def main():
     args = parse()
     from paper_2109_04469_gb300 import workloads
@@ -216,106 +310,58 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    from paper_2109_04469_gb300 import pic
-
     cfg["instance"] = rank  # independent replica per rank
     pcfg = {k: v for k, v in cfg.items() if k != "name"}
-    sim = pic.Simulation(pcfg)
-    stream = sim.stream
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    sim.step(args.warmup)
-    sim.sync()
-    c0 = sim.accum()["counters"].astype(np.int64)
-    d = sim.derived()
-    try:
-        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
-        uuid = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
-    except Exception:
-        uuid = None
-    sampler = ClockSampler(uuid)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    ms2 = np.zeros(2)  # particle pass, compaction (+ next field solve beside it)
-    step_ms = 0.0
-    parts = 0
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(k)  # L2 flush between timed steps (outside the events)
-            ne, ni = sim.counts()
-            parts += ne + ni
-            ev0.record(stream)
-            sim.step_profiled(1, ms2)
-            ev1.record(stream)
-            ev1.synchronize()
-            step_ms += ev0.elapsed_time(ev1)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    # the field solve on its own (it runs beside the compaction inside each step)
-    field_ms = 0.0
-    with torch.cuda.stream(stream):
-        for k in range(10):
-            ev0.record(stream)
-            sim.solve_field()
-            ev1.record(stream)
-            ev1.synchronize()
-            field_ms += ev0.elapsed_time(ev1) / 10
-    status = sim.status()
-    c1 = sim.accum()["counters"].astype(np.int64)
-    dc = c1 - c0
-    # algorithmic bytes of the particle pass (per particle-step: x, vx r/w + id read = 36 B;
-    # candidates r/w vy, vz 32 B; removed and born particles move one 36 B record)
-    turnover = int(dc[0] + dc[1] + dc[2] + dc[3] + 2 * dc[8] + dc[5])
-    alg_bytes = 36.0 * parts + 32.0 * float(dc[11] + dc[12]) + 36.0 * turnover
-    total_ms = step_ms
-    total_parts = parts
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        p = torch.tensor([float(total_parts)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        total_parts = int(p.item())
+    runs = {}
+    for prec in args.precisions.split(","):
+        runs[prec] = measure(pcfg, prec, args, torch, dist, local_rank,
+                             with_e2e=(prec == args.precisions.split(",")[0] and not args.no_e2e))
+    head_prec = args.precisions.split(",")[0]
+    head = runs[head_prec]
+    total_ms, total_parts = reduce_ranks(torch, dist, head["step_ms"], head["parts"])
     value = total_parts / (total_ms / 1e3)
-    push_ms = ms2[0] / args.steps
-    compact_ms = ms2[1] / args.steps
     peak, peak_src = measured_peak()
-    achieved = (alg_bytes / args.steps) / (push_ms / 1e3) / 1e9
+    achieved = head["alg_bytes_per_launch"] / (head["push_ms"] / 1e3) / 1e9
+    kname = "k_push_fp32" if head_prec == "fp32" else "k_push_fp64"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
-            "traffic": profiled_traffic("push_fp64", args.workload),
-            "kernel": "k_push_fp64", "alg_bytes_per_launch": alg_bytes / args.steps,
-            "launch_ms": push_ms}
-
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(sim, args, torch)
+            "traffic": profiled_traffic(f"push_{head_prec}", args.workload),
+            "kernel": kname, "alg_bytes_per_launch": head["alg_bytes_per_launch"],
+            "launch_ms": head["push_ms"]}
+    ms_step = total_ms / args.steps
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if head_prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "particles_per_species": cfg["init_per_species"],
                        "n_cells": cfg["n_cells"], "steps_per_rf": cfg["steps_per_rf"],
-                       "precision": "fp64", "parallelism": f"replicas x{world}",
+                       "precision": head_prec + (" particles, fp64 field" if head_prec == "fp32"
+                                                 else ""),
+                       "parallelism": f"replicas x{world}",
                        "l2": "flushed (256 MiB write) between timed steps"},
             "roofline": roof,
-            "kernel_ms_per_step": {"particles": push_ms, "compaction_and_next_field": compact_ms,
-                                   "field_alone": field_ms},
-            "poisson_share": field_ms / (total_ms / args.steps),
-            "compaction_share": compact_ms / (total_ms / args.steps),
+            "kernel_ms_per_step": {"particles": head["push_ms"],
+                                   "placement_and_next_field": head["place_ms"],
+                                   "field_alone": head["field_ms"]},
+            "poisson_share": head["field_ms"] / ms_step,
+            "compaction_share": max(0.0, head["place_ms"] - head["field_ms"]) / ms_step,
             "gpu_launches": 2 * args.steps,
-            "clocks": clocks, "status": status}
-    if e2e:
-        line["e2e"] = e2e
+            "clocks": head["clocks"], "status": head["status"]}
+    for prec, r in runs.items():
+        if prec == head_prec:
+            continue
+        t, p = reduce_ranks(torch, dist, r["step_ms"], r["parts"])
+        line[f"{prec}_plain"] = {
+            "value": p / (t / 1e3), "ms_per_step": t / args.steps, "particles_ms": r["push_ms"],
+            "roofline_frac_hbm": r["alg_bytes_per_launch"] / (r["push_ms"] / 1e3) / 1e9 / peak,
+            "clocks": r["clocks"]}
+        line[f"speedup_vs_{prec}"] = value / (p / (t / 1e3))
+    if "e2e" in head:
+        line["e2e"] = head["e2e"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pcfg | {"name": args.workload}, args.cpu_steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sim.close()
     if dist:
         dist.destroy_process_group()
 

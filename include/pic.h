@@ -30,6 +30,7 @@ extern "C" {
 #define PIC_ERR_CAPACITY (-3)   /* births exceeded capacity_per_species; excess dropped */
 #define PIC_ERR_NONFINITE (-4)  /* a velocity became NaN or infinite */
 #define PIC_ERR_WORKSPACE (-5)  /* workspace missing, too small or misaligned */
+#define PIC_ERR_TIMEOUT (-6)    /* a bounded device wait ran out; results of the step invalid */
 #define PIC_WARN_UNSTABLE 1     /* omega_pe*dt > 2: the leapfrog stability bound of §3.5 */
 
 #define PIC_FP64 0 /* FP64 particle state; bit-for-bit the oracle's step contract */

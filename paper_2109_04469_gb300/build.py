@@ -20,6 +20,9 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-I", os.path.join(ROOT, "include"),
 UNITS = {
     "pic_fp64.cu": ["-fmad=false"],
     "pic_capi.cu": ["-fmad=false"],
+    # statistical FP32 path: contraction allowed (its FP64 field solve uses explicit
+    # round-to-nearest intrinsics)
+    "pic_fp32.cu": [],
 }
 
 
@@ -46,11 +49,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _sources_newer_than(LIB):
         return LIB
     exe = nvcc()
+    extra_env = os.environ.get("PIC_NVCC_FLAGS", "").split()  # tuning sweeps only
     procs = []
     objs = []
     for src, extra in UNITS.items():
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [exe, *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [exe, *ARCH, *COMMON, *extra, *extra_env, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -133,7 +133,8 @@ bool valid(const pic_params* p) {
          p->area_m2 > 0 && p->init_te_ev >= 0 && p->see_energy_ev >= 0 &&
          p->init_per_species >= 0 && p->capacity_per_species >= p->init_per_species &&
          p->capacity_per_species >= 1 && p->capacity_per_species < (int64_t(1) << 31) - kChunk &&
-         (p->precision == PIC_FP64) && p->eepf_bins >= 1 && p->eepf_bins <= (1 << 20) &&
+         (p->precision == PIC_FP64 || p->precision == PIC_FP32) && p->eepf_bins >= 1 &&
+         p->eepf_bins <= (1 << 20) &&
          p->eepf_emax_ev > 0 && p->fedf_bins >= 1 && p->fedf_bins <= (1 << 20) &&
          p->fedf_emax_ev > 0;
 }
@@ -151,6 +152,10 @@ struct Carver {
   }
 };
 
+// Upper bound of the particle grid size (entries of the per-block count arrays).
+// (FP32 handles keep one list per warp: 8 per block of at most capacity/256 blocks.)
+long long max_list_blocks(const pic_params& p) { return p.capacity_per_species / 32 + 8192; }
+
 void carve(const pic_params& p, char* base, DevCtx& K, size_t* total) {
   Carver c{base};
   const int nx = p.n_cells + 1;
@@ -158,12 +163,13 @@ void carve(const pic_params& p, char* base, DevCtx& K, size_t* total) {
   const size_t cap = (size_t)nch * kChunk;
   K.nchunk_max = nch;
   K.st = c.take<DevState>(1);
+  K.self = c.take<DevCtx>(1);
   for (int s = 0; s < 2; ++s) {
     K.x[s] = c.take<double>(cap);
     K.vx[s] = c.take<double>(cap);
     K.vy[s] = c.take<double>(cap);
     K.vz[s] = c.take<double>(cap);
-    K.id[s] = c.take<unsigned>(cap);
+    K.id[s] = c.take<unsigned>(cap + 64);  // tail padding for rounded bulk copies
   }
   K.C = c.take<unsigned long long>((size_t)4 * nx);
   K.phi = c.take<double>(nx);
@@ -176,19 +182,35 @@ void carve(const pic_params& p, char* base, DevCtx& K, size_t* total) {
   K.eepf = c.take<unsigned long long>((size_t)p.eepf_bins);
   K.fedf = c.take<unsigned long long>((size_t)2 * p.fedf_bins);
   K.counters = c.take<unsigned long long>(kNumCounters);
-  // per-block list counts: any particle grid has at most 2 * nch blocks
-  const size_t nl = (size_t)2 * nch + 8;
+  // per-block list counts: the particle grid has at most max_list_blocks(p) blocks
+  const size_t nl = (size_t)max_list_blocks(p);
+  const bool fp32 = p.precision == PIC_FP32;
   for (int s = 0; s < 2; ++s) {
     K.hole_idx[s] = c.take<int>(cap);
     K.hole_cnt[s] = c.take<int>(nl);
     K.hole_pref[s] = c.take<int>(nl);
     K.eb_cnt[s] = c.take<int>(nl);
     K.eb_pref[s] = c.take<int>(nl);
-    K.eb[s] = c.take<double>(4 * cap);
+    K.eb[s] = fp32 ? nullptr : c.take<double>(4 * cap);
   }
   K.ib_cnt = c.take<int>(nl);
   K.ib_pref = c.take<int>(nl);
-  K.ib = c.take<double>(4 * cap);
+  K.ib = fp32 ? nullptr : c.take<double>(4 * cap);
+  if (fp32) {
+    for (int s = 0; s < 2; ++s) {
+      // 64 elements of tail padding: a bulk copy of a last tile is rounded up to 16 bytes
+      K.cell[s] = c.take<unsigned short>(cap + 64);
+      K.cdown[s] = c.take<unsigned short>(cap + 64);
+      K.off[s] = c.take<float>(cap + 64);
+      K.fvx[s] = c.take<float>(cap + 64);
+      K.fvy[s] = c.take<float>(cap);
+      K.fvz[s] = c.take<float>(cap);
+      K.feb[s] = c.take<float>(6 * cap);
+      K.fF[s] = c.take<float>((size_t)kXsNodes * 4);
+      K.fE[s] = c.take<float>(nx);
+    }
+    K.fib = c.take<float>(6 * cap);
+  }
   *total = (c.off + 255) & ~size_t(255);
 }
 
@@ -199,7 +221,15 @@ unsigned long long null_threshold(double pmax) {
   return (unsigned long long)c / 2ull;
 }
 
+// FP32 path: u = (2k+1) 2^-25 with k a 24-bit integer; u < P_max <=> k < floor(C/2),
+// C = ceil(P_max 2^25).
+unsigned null_threshold24(double pmax) {
+  const double c = std::ceil(std::ldexp(pmax, 25));
+  return (unsigned)((unsigned long long)c / 2ull);
+}
+
 int status_code(int st) {
+  if (st & kStTimeout) return PIC_ERR_TIMEOUT;
   if (st & kStNonfinite) return PIC_ERR_NONFINITE;
   if (st & kStCapacity) return PIC_ERR_CAPACITY;
   return PIC_OK;
@@ -218,6 +248,20 @@ struct pic_handle {
   int place_grid;
   int last_status;
 };
+
+namespace {
+bool is_fp32(const pic_handle* h) { return h->p.precision == PIC_FP32; }
+
+cudaError_t launch_particles(const pic_handle* h) {
+  return is_fp32(h) ? launch_push_fp32(h->K, h->push_grid, h->stream)
+                    : launch_push_fp64(h->K, h->push_grid, h->stream);
+}
+
+cudaError_t launch_place(const pic_handle* h) {
+  return is_fp32(h) ? launch_place_fp32(h->K, h->place_grid, h->stream)
+                    : launch_place_fp64(h->K, h->place_grid, h->stream);
+}
+}  // namespace
 
 #define PIC_CUDA(call)                        \
   do {                                        \
@@ -311,6 +355,31 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   K.fedf_inv_de = (double)p->fedf_bins / p->fedf_emax_ev;
   K.key0 = (unsigned)p->seed;
   K.key1 = (unsigned)(p->seed >> 32) ^ p->instance;
+  const bool fp32 = p->precision == PIC_FP32;
+  std::vector<float> fFe, fFi;
+  if (fp32) {  // cell units: x / dx, v dt / dx
+    const double vs = d.dt * d.inv_dx, vs2 = vs * vs;
+    K.f_emfac_e = (float)(d.emfac_e / vs2);
+    K.f_emfac_rel = (float)(d.emfac_rel / vs2);
+    K.f_emfac_ilab = (float)(d.emfac_ilab / vs2);
+    K.f_spd2_e = (float)(d.spd2_e * vs2);
+    K.f_sig_i = (float)(d.sig_i * vs);
+    K.f_v_see = (float)(d.v_see * vs);
+    K.f_mr2 = (float)d.mr2;
+    K.f_refl = (float)p->refl_e;
+    K.f_gamma = (float)p->gamma_see;
+    K.f_eepf_inv_de = (float)K.eepf_inv_de;
+    K.f_fedf_inv_de = (float)K.fedf_inv_de;
+    K.f_null_thr[0] = null_threshold24(d.pmax[0]);
+    K.f_null_thr[1] = null_threshold24(d.pmax[1]);
+    K.f_lnq[0] = (float)std::log1p(-d.pmax[0]);  // geometric countdown of the FP32 pass
+    K.f_lnq[1] = (float)std::log1p(-d.pmax[1]);
+    K.to_si_v = d.dx / d.dt;
+    K.fe_scale[0] = d.qm_dt[0] * d.dt * d.inv_dx;  // E -> kick in cells per step
+    K.fe_scale[1] = d.qm_dt[1] * d.dt * d.inv_dx;
+    fFe.assign(Fe.begin(), Fe.end());
+    fFi.assign(Fi.begin(), Fi.end());
+  }
   h->K = K;
 
   int dev = 0, sms = 0;
@@ -322,13 +391,17 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   };
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      configure_kernels(nx) != cudaSuccess)
+      configure_kernels(nx) != cudaSuccess || (fp32 && configure_kernels32(nx) != cudaSuccess))
     return fail(PIC_ERR_CUDA);
-  const int bps = push_fp64_blocks_per_sm(nx);
-  h->push_grid = std::max(1, std::min(2 * K.nchunk_max, sms * bps));
+  // persistent particle grid: resident blocks on all SMs, fewer for small populations
+  const int bps = fp32 ? push_fp32_blocks_per_sm(nx) : push_fp64_blocks_per_sm(nx);
+  const long long by_size = (p->capacity_per_species + 255) / 256;
+  h->push_grid = (int)std::max(1LL, std::min<long long>({(long long)sms * bps, by_size,
+                                                          max_list_blocks(*p) / 8}));
   h->place_grid = 1 + sms;
-  K.nlist = h->push_grid;
-  h->K.nlist = h->push_grid;
+  // hole / birth list owners: particle blocks (FP64 pass) or their warps (FP32 pass)
+  K.nlist = fp32 ? h->push_grid * (kBlock / 32) : h->push_grid;
+  h->K.nlist = K.nlist;
 
   DevState s0;
   std::memset(&s0, 0, sizeof s0);
@@ -344,11 +417,22 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
       cudaMemcpyAsync((void*)K.F[0], Fe.data(), sizeof(double) * Fe.size(),
                       cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync((void*)K.F[1], Fi.data(), sizeof(double) * Fi.size(),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      // the device copy of the context (read by out-of-line device functions)
+      cudaMemcpyAsync((void*)K.self, &h->K, sizeof(DevCtx), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return fail(PIC_ERR_CUDA);
+  if (fp32 && (cudaMemcpyAsync((void*)K.fF[0], fFe.data(), sizeof(float) * fFe.size(),
+                               cudaMemcpyHostToDevice, st) != cudaSuccess ||
+               cudaMemcpyAsync((void*)K.fF[1], fFi.data(), sizeof(float) * fFi.size(),
+                               cudaMemcpyHostToDevice, st) != cudaSuccess))
     return fail(PIC_ERR_CUDA);
   for (int s = 0; s < 2; ++s) {
+    // the FP32 state is the FP64 load rounded, so both precisions start from one sample
     if (launch_init_load(K, s, p->init_per_species, st) != cudaSuccess ||
-        launch_deposit(K, s, 0, p->init_per_species, st) != cudaSuccess)
+        (fp32 ? (launch_convert(K, s, p->init_per_species, true, st) != cudaSuccess ||
+                 launch_deposit32(K, s, 0, p->init_per_species, st) != cudaSuccess)
+              : launch_deposit(K, s, 0, p->init_per_species, st) != cudaSuccess))
       return fail(PIC_ERR_CUDA);
   }
   if (launch_field(K, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
@@ -360,8 +444,7 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
 int pic_step(pic_handle* h, int64_t n_steps) {
   if (!h || n_steps < 0) return PIC_ERR_PARAM;
   for (int64_t i = 0; i < n_steps; ++i) {
-    if (launch_push_fp64(h->K, h->push_grid, h->stream) != cudaSuccess ||
-        launch_place_fp64(h->K, h->place_grid, h->stream) != cudaSuccess) {
+    if (launch_particles(h) != cudaSuccess || launch_place(h) != cudaSuccess) {
       (void)cudaGetLastError();
       return PIC_ERR_CUDA;
     }
@@ -382,9 +465,9 @@ int pic_step_profiled(pic_handle* h, int64_t n_steps, double* ms_out) {
   for (int64_t i = 0; i < n_steps && rc == PIC_OK; ++i) {
     float t[2];
     if (cudaEventRecord(ev[0], h->stream) != cudaSuccess ||
-        launch_push_fp64(h->K, h->push_grid, h->stream) != cudaSuccess ||
+        launch_particles(h) != cudaSuccess ||
         cudaEventRecord(ev[1], h->stream) != cudaSuccess ||
-        launch_place_fp64(h->K, h->place_grid, h->stream) != cudaSuccess ||
+        launch_place(h) != cudaSuccess ||
         cudaEventRecord(ev[2], h->stream) != cudaSuccess ||
         cudaEventSynchronize(ev[2]) != cudaSuccess ||
         cudaEventElapsedTime(&t[0], ev[0], ev[1]) != cudaSuccess ||
@@ -445,6 +528,7 @@ int pic_get_particles(pic_handle* h, int species, double* x, double* vx, double*
   if (m > 0) {
     const DevCtx& K = h->K;
     cudaStream_t st = h->stream;
+    if (is_fp32(h)) PIC_CUDA(launch_convert(K, species, n, false, st));
     if (x) PIC_CUDA(cudaMemcpyAsync(x, K.x[species], m * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (vx) PIC_CUDA(cudaMemcpyAsync(vx, K.vx[species], m * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (vy) PIC_CUDA(cudaMemcpyAsync(vy, K.vy[species], m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -480,7 +564,12 @@ int pic_set_particles(pic_handle* h, int species, const double* x, const double*
   const int buf = s.step & 1;
   PIC_CUDA(cudaMemsetAsync(K.C + (size_t)(buf * 2 + species) * K.nx, 0,
                            sizeof(unsigned long long) * K.nx, st));
-  PIC_CUDA(launch_deposit(K, species, buf, n, st));
+  if (is_fp32(h)) {
+    PIC_CUDA(launch_convert(K, species, n, true, st));
+    PIC_CUDA(launch_deposit32(K, species, buf, n, st));
+  } else {
+    PIC_CUDA(launch_deposit(K, species, buf, n, st));
+  }
   PIC_CUDA(launch_field(K, st));
   PIC_CUDA(cudaStreamSynchronize(st));
   return PIC_OK;
@@ -556,6 +645,14 @@ int pic_override_table(pic_handle* h, int species, const double* table, double n
   h->d.pmax[species] = 1.0 - std::exp(-nu_max * h->d.dt);
   h->K.pmax[species] = h->d.pmax[species];
   h->K.null_kthr[species] = null_threshold(h->d.pmax[species]);
+  if (is_fp32(h)) {
+    std::vector<float> f(table, table + (size_t)kXsNodes * 4);
+    PIC_CUDA(cudaMemcpy((void*)h->K.fF[species], f.data(), sizeof(float) * f.size(),
+                        cudaMemcpyHostToDevice));
+    h->K.f_null_thr[species] = null_threshold24(h->d.pmax[species]);
+    h->K.f_lnq[species] = (float)std::log1p(-h->d.pmax[species]);
+    PIC_CUDA(cudaMemcpy((void*)h->K.self, &h->K, sizeof(DevCtx), cudaMemcpyHostToDevice));
+  }
   return PIC_OK;
 }
 
@@ -588,6 +685,7 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
   // max |vx| over the electrons for the CFL number
   PIC_CUDA(cudaMemsetAsync(&K.st->vmax_bits, 0, sizeof(unsigned long long), h->stream));
+  if (is_fp32(h)) PIC_CUDA(launch_convert(K, 0, s.n[0], false, h->stream));
   PIC_CUDA(launch_max_abs(K.vx[0], s.n[0], &K.st->vmax_bits, h->stream));
   unsigned long long vbits = 0;
   PIC_CUDA(cudaStreamSynchronize(h->stream));
@@ -671,6 +769,7 @@ const char* pic_strerror(int code) {
     case PIC_ERR_CAPACITY: return "particle capacity exceeded (births dropped)";
     case PIC_ERR_NONFINITE: return "non-finite particle velocity";
     case PIC_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+    case PIC_ERR_TIMEOUT: return "a bounded device wait ran out (staged data never arrived)";
     case PIC_WARN_UNSTABLE: return "omega_pe*dt above the leapfrog stability bound 2";
     default: return "unknown code";
   }

@@ -238,14 +238,28 @@ __device__ __forceinline__ int lower_bound_i(const int* a, int n, long long v) {
 // Run by the last particle block to finish (after a fence): exclusive prefixes of the five
 // per-block count arrays in one block scan, the totals of reading C-15 for both species,
 // the new counts and ids.  NW = warps of the block.
+// scratch: free shared memory of the block (scratch_ints ints); when it holds the five count
+// arrays they are first staged there with coalesced loads, so the serial per-thread segments
+// read shared memory instead of waiting on one global load after another.
 template <int NW>
-__device__ void finalize_compaction(const DevCtx& K, long long ne, long long ni) {
+__device__ void finalize_compaction(const DevCtx& K, long long ne, long long ni, int* scratch,
+                                    int scratch_ints) {
   constexpr int kA = 5;
   __shared__ int wsum[NW][kA], wtot[kA];
   __shared__ long long sq[2];
-  const int G = gridDim.x;
-  int* cnt[kA] = {K.hole_cnt[0], K.hole_cnt[1], K.eb_cnt[0], K.eb_cnt[1], K.ib_cnt};
+  const int G = K.nlist;  // list owners: particle blocks (FP64 pass) or warps (FP32 pass)
+  int* gcnt[kA] = {K.hole_cnt[0], K.hole_cnt[1], K.eb_cnt[0], K.eb_cnt[1], K.ib_cnt};
   int* pref[kA] = {K.hole_pref[0], K.hole_pref[1], K.eb_pref[0], K.eb_pref[1], K.ib_pref};
+  const int* cnt[kA];
+  if (kA * G <= scratch_ints) {
+    for (int i = threadIdx.x; i < kA * G; i += blockDim.x) scratch[i] = gcnt[i / G][i % G];
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < kA; ++a) cnt[a] = scratch + a * G;
+  } else {
+#pragma unroll
+    for (int a = 0; a < kA; ++a) cnt[a] = gcnt[a];
+  }
   const int seg = (G + blockDim.x - 1) / blockDim.x;
   const int c0 = min((int)threadIdx.x * seg, G), c1 = min(c0 + seg, G);
   int loc[kA];

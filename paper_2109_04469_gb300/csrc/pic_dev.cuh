@@ -19,7 +19,7 @@ constexpr int kNumCounters = 16;
 constexpr double kEExc = 11.55;    // eV, lumped excitation threshold
 constexpr double kEIon = 15.76;    // eV, ionization threshold (§3.1)
 
-enum : int { kStCapacity = 1, kStNonfinite = 2 };
+enum : int { kStCapacity = 1, kStNonfinite = 2, kStTimeout = 4 };
 enum : int { kPurStep = 0, kPurColl = 1, kPurEmit = 2, kPurLoad = 3 };
 enum : int {
   kCnEAbsL = 0, kCnEAbsR, kCnIAbsL, kCnIAbsR, kCnERefl, kCnSee, kCnEEla, kCnEExc, kCnEIon,
@@ -111,6 +111,23 @@ struct DevCtx {
   int *ib_cnt, *ib_pref;        // ion births from blocks' electron chunks
   double *eb[2];        // [4][cap] records x, vx, vy, vz of electron births (FP64 state)
   double *ib;           // [4][cap] ion births (FP64 state)
+  // FP32 particle state (precision PIC_FP32): position = cell + off in cells, off in [0, 1]
+  // (1 only for a particle born on x = L), velocities in cells per step
+  unsigned short* cell[2];
+  unsigned short* cdown[2];  // steps to the next null-collision candidate (bit 15: none)
+  float *off[2], *fvx[2], *fvy[2], *fvz[2];
+  float *feb[2], *fib;  // [6][cap] birth records: cell (int bits), off, vx, vy, vz, countdown
+  float f_lnq[2];       // ln(1 - P_max) per species (0 without gas)
+  const float* fF[2];   // FP32 cumulative collision fractions [kXsNodes][4]
+  float f_emfac_e, f_emfac_rel, f_emfac_ilab;  // (cells/step)^2 -> eV
+  float f_spd2_e;                              // eV -> (cells/step)^2 of an electron
+  float f_sig_i, f_v_see, f_mr2;               // thermal ion speed, emitted speed, 2m/M
+  float f_refl, f_gamma, f_eepf_inv_de, f_fedf_inv_de;
+  unsigned f_null_thr[2];  // u < P_max <=> (w >> 8) < f_null_thr for u = (2k+1) 2^-25
+  double to_si_v;          // cells/step -> m/s
+  // a copy of this struct in device memory, for out-of-line device functions (taking the
+  // address of a kernel parameter would copy the struct into every thread's local memory)
+  const struct DevCtx* self;
 };
 
 // ------------------------------------------------------------------ Philox4x32-10

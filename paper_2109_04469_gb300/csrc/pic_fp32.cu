@@ -1,0 +1,666 @@
+// pic_fp32.cu -- FP32 particle path of one PIC/MCC timestep (arXiv 2109.04469, §2 steps
+// 3-6 and the deposit of step 1), GB300.
+//
+// Particles are stored as a 16-bit cell index plus an FP32 offset in the cell and FP32
+// velocities in cells per step, so the push is one kick and one drift per particle:
+//   vx += kick(x),  off += vx,  cell += floor(off),  off -= floor(off).
+// The field solve stays FP64 (pic_common.cuh) and writes the kick table fE[s][j] =
+// (q/m) dt^2/dx E_j.  The deposit uses 16-bit linear weights accumulated in block-private
+// 32-bit shared counters and flushed (<< 16) into the same int64 grid as the FP64 path, so
+// charge stays exact and order-free.  Compaction and births follow the same hole-filling
+// rule (reading C-15) through the common placement launch.  Results are statistical
+// matches of the FP64 oracle, not bitwise ones.
+//
+// Null collisions (§3.5, reading C-7): a per-step Bernoulli(P_max) candidate test is the same
+// in distribution as a geometric waiting time between candidates, so each particle carries a
+// 16-bit countdown of the steps to its next candidate, drawn again at every candidate.  The
+// counter-based generator then runs only at candidates, surfaces and births.
+//
+// Work split: every warp owns a contiguous, balanced range of each species and walks it in
+// 128-particle tiles staged in shared memory by bulk asynchronous copies (kStages - 1 tiles
+// in flight per warp), with particle p = tile + 32 k + lane (k = 0..3): ranking holes and
+// births with ballot/popc per k is already particle order, so warps never wait for one
+// another.  The hole and birth lists are per warp.  The rare branches (surfaces, collisions,
+// EEPF samples) are out-of-line calls so the hot loop stays small.
+#include <cuda_runtime.h>
+
+#include "pic_common.cuh"
+#include "pic_dev.cuh"
+#include "pic_launch.h"
+#include "pic_tma.cuh"
+
+namespace pic {
+
+// Resident blocks per SM the particle pass is compiled for (register budget 65536 /
+// (256 x this)); the rare out-of-line branches may spill under a tight budget.
+#ifndef PIC_FP32_MIN_BLOCKS
+#define PIC_FP32_MIN_BLOCKS 2
+#endif
+
+constexpr int kWarps32 = kBlock / 32;
+constexpr int kRoundPerWarp = 4096;  // particles a warp handles between counter flushes
+// 8 warps x 4096 particles x (a particle + a birth) x 2^16 < 2^32: the 32-bit counters of a
+// block cannot overflow between flushes.
+constexpr unsigned short kCdFlag = 0x8000;  // countdown expires without a candidate
+constexpr int kPurCount = 4;                 // stream purpose: countdown of a new particle
+
+__device__ __forceinline__ float u24(unsigned w) {  // (2k+1) 2^-25, k = top 24 bits
+  return (float)((w >> 8) * 2u + 1u) * 0x1p-25f;
+}
+
+// Steps to the next null-collision candidate of a per-step Bernoulli(P) trial (geometric,
+// >= 1), from a uniform u in (0, 1) and lnq = ln(1 - P) < 0.  Waits beyond 32766 steps are
+// split: the countdown then expires with the flag set and is drawn again (memoryless).
+__device__ __forceinline__ unsigned short draw_countdown(float u, float lnq) {
+  if (!(lnq < 0.0f)) return (unsigned short)(kCdFlag | 0x7FFF);
+  const float t = floorf(logf(u) / lnq);
+  if (!(t < 32766.0f)) return (unsigned short)(kCdFlag | 0x7FFF);
+  return (unsigned short)(t + 1.0f);
+}
+
+// Uniform direction (Marsaglia 1972); each Philox block offers two attempts.
+__device__ __forceinline__ void iso_dir_f(Stream& st, float& n0, float& n1, float& n2) {
+  for (int a = 0; a < kMaxTries / 2; ++a) {
+    const U4 w = philox4x32_10(st.id, st.step, st.base | st.block, 0u, st.k0, st.k1);
+    ++st.block;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float v1 = 2.0f * u24(h ? w.c : w.a) - 1.0f, v2 = 2.0f * u24(h ? w.d : w.b) - 1.0f;
+      const float s = v1 * v1 + v2 * v2;
+      if (s < 1.0f) {
+        const float q = 2.0f * sqrtf(1.0f - s);
+        n0 = v1 * q;
+        n1 = v2 * q;
+        n2 = 1.0f - 2.0f * s;
+        return;
+      }
+    }
+  }
+  n0 = 0.0f; n1 = 0.0f; n2 = 1.0f;
+}
+
+// Two standard normal deviates (Marsaglia polar method).
+__device__ __forceinline__ void gauss_pair_f(Stream& st, float& g0, float& g1) {
+  for (int a = 0; a < kMaxTries / 2; ++a) {
+    const U4 w = philox4x32_10(st.id, st.step, st.base | st.block, 0u, st.k0, st.k1);
+    ++st.block;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float v1 = 2.0f * u24(h ? w.c : w.a) - 1.0f, v2 = 2.0f * u24(h ? w.d : w.b) - 1.0f;
+      const float s = v1 * v1 + v2 * v2;
+      if (s < 1.0f) {
+        const float fac = sqrtf(-2.0f * logf(s) / s);
+        g0 = v1 * fac;
+        g1 = v2 * fac;
+        return;
+      }
+    }
+  }
+  g0 = 0.0f; g1 = 0.0f;
+}
+
+__device__ __forceinline__ float next_u(Stream& st) {  // one more uniform of a stream
+  const U4 w = philox4x32_10(st.id, st.step, st.base | st.block, 0u, st.k0, st.k1);
+  ++st.block;
+  return u24(w.a);
+}
+
+__device__ __forceinline__ void lookup_f(const float* __restrict__ F, float eps, float& f0,
+                                         float& f1, float& f2) {
+  const float t = eps * (float)kXsInvDe;
+  if (!(t < (float)(kXsNodes - 1))) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(F) + (kXsNodes - 1));
+    f0 = a.x; f1 = a.y; f2 = a.z;
+    return;
+  }
+  const int k = (int)t;  // t >= 0
+  const float fr = t - (float)k;
+  const float4 a = __ldg(reinterpret_cast<const float4*>(F) + k);
+  const float4 b = __ldg(reinterpret_cast<const float4*>(F) + k + 1);
+  f0 = a.x + fr * (b.x - a.x);
+  f1 = a.y + fr * (b.y - a.y);
+  f2 = a.z + fr * (b.z - a.z);
+}
+
+// 16-bit linear weights into the block's 32-bit counters (w_L + w_R = 2^16 exactly).
+__device__ __forceinline__ void deposit32(unsigned* C, int j, float f) {
+  const int wr = __float2int_rn(f * 65536.0f);
+  atomicAdd(&C[j], (unsigned)(65536 - wr));
+  atomicAdd(&C[j + 1], (unsigned)wr);
+}
+
+// (cell, off) with off brought back into [0, 1)
+__device__ __forceinline__ void renorm(int& c, float& off) {
+  const float k = floorf(off);
+  c += (int)k;
+  off -= k;
+}
+
+// A birth: position and velocity in cell units, countdown.
+struct Rec32 {
+  int cell;
+  float off, vx, vy, vz;
+  unsigned cd;
+};
+
+struct SurfOut {  // state after step 5; flags: bit 0 removed, bit 1 electron emitted
+  int cell;
+  float off, vx;
+  int flags;
+};
+
+// Step 5 for a particle that left the gap (x <= 0 or x >= L).  An emitted electron is
+// written to *em (this lane's slot in shared memory).
+template <int S>
+__device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned step, long long p,
+                                          unsigned pid, int cell, float off, float vx, bool left,
+                                          unsigned* sCe, unsigned long long* sCnt, Rec32* em) {
+  const int nc = G->nc;
+  // the per-step block of the FP64 contract: its third word decides the surface event
+  const U4 w = philox4x32_10(pid, step, ((unsigned)S << 30) | ((unsigned)kPurStep << 24), 0u,
+                             G->key0, G->key1);
+  const float u_wall = u24(w.c);
+  if (S == 0) {
+    if (u_wall < G->f_refl) {  // specular reflection
+      if (off > 0.0f) {
+        cell = left ? -cell - 1 : 2 * nc - cell - 1;
+        off = 1.0f - off;
+      } else {
+        cell = left ? -cell : 2 * nc - cell;
+      }
+      renorm(cell, off);
+      vx = -vx;
+      atomicAdd(&sCnt[kCnERefl], 1ull);
+      if (!(cell < 0 || (cell == 0 && off == 0.0f) || cell >= nc)) return SurfOut{cell, off, vx, 0};
+    }
+    atomicAdd(&sCnt[left ? kCnEAbsL : kCnEAbsR], 1ull);
+    const float vy = G->fvy[S][p], vz = G->fvz[S][p];
+    const float t = (vx * vx + vy * vy + vz * vz) * G->f_emfac_e * G->f_fedf_inv_de;
+    if (t < (float)G->fedf_bins) atomicAdd(&G->fedf[(int)t], 1ull);
+    return SurfOut{cell, off, vx, 1};
+  }
+  atomicAdd(&sCnt[left ? kCnIAbsL : kCnIAbsR], 1ull);
+  const float vy = G->fvy[S][p], vz = G->fvz[S][p];
+  const float t = (vx * vx + vy * vy + vz * vz) * G->f_emfac_ilab * G->f_fedf_inv_de;
+  if (t < (float)G->fedf_bins) atomicAdd(&G->fedf[G->fedf_bins + (int)t], 1ull);
+  int flags = 1;
+  if (u_wall < G->f_gamma) {  // ion-induced electron at the struck electrode
+    Stream se(*G, 1, kPurEmit, pid, step);
+    float n0, n1, n2;
+    iso_dir_f(se, n0, n1, n2);
+    const float ax = fabsf(n0) * G->f_v_see;
+    Rec32 r;
+    r.cell = left ? 0 : nc - 1;
+    r.off = left ? 0.0f : 1.0f;
+    r.vx = left ? ax : -ax;
+    r.vy = n1 * G->f_v_see;
+    r.vz = n2 * G->f_v_see;
+    r.cd = draw_countdown(next_u(se), G->f_lnq[0]);
+    *em = r;
+    flags |= 2;
+    deposit32(sCe, r.cell, r.off);
+    atomicAdd(&sCnt[kCnSee], 1ull);
+  }
+  return SurfOut{cell, off, vx, flags};
+}
+
+struct CollOut {  // state after step 6; born: an ionization pair was written
+  float vx;
+  unsigned cd;
+  int born;
+};
+
+// Countdown expiry: a null-collision candidate unless the flag is set (readings C-7..C-10,
+// C-13), then the next countdown.  An ionization writes the pair to *re / *ri (this lane's
+// slots in shared memory).
+template <int S>
+__device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned step, long long p,
+                                          unsigned pid, int cell, float off, float vx,
+                                          unsigned cd, unsigned* sCe, unsigned* sCi,
+                                          unsigned long long* sCnt, Rec32* re, Rec32* ri) {
+  Stream sc(*G, S, kPurColl, pid, step);
+  const U4 wp = philox4x32_10(sc.id, sc.step, sc.base | sc.block, 0u, sc.k0, sc.k1);
+  ++sc.block;
+  const bool candidate = !(cd & kCdFlag);
+  const unsigned cd_next = draw_countdown(u24(wp.b), G->f_lnq[S]);
+  if (!candidate) return CollOut{vx, cd_next, 0};
+  float vy = G->fvy[S][p], vz = G->fvz[S][p];
+  bool dirty = false;
+  int born = 0;
+  const float up = u24(wp.a);
+  if (S == 0) {
+    atomicAdd(&sCnt[kCnECand], 1ull);
+    const float v2 = vx * vx + vy * vy + vz * vz;
+    const float eps = v2 * G->f_emfac_e;
+    float F0, F1, F2;
+    lookup_f(G->fF[0], eps, F0, F1, F2);
+    if (up < F0) {  // elastic (C-9)
+      float n0, n1, n2;
+      iso_dir_f(sc, n0, n1, n2);
+      const float vmag = sqrtf(v2);
+      const float cosx = vmag > 0.0f ? (vx * n0 + vy * n1 + vz * n2) / vmag : 0.0f;
+      const float sp = vmag * sqrtf(1.0f - G->f_mr2 * (1.0f - cosx));
+      vx = n0 * sp; vy = n1 * sp; vz = n2 * sp;
+      dirty = true;
+      atomicAdd(&sCnt[kCnEEla], 1ull);
+    } else if (up < F1) {  // excitation
+      if (eps >= (float)kEExc) {
+        float n0, n1, n2;
+        iso_dir_f(sc, n0, n1, n2);
+        const float sp = sqrtf((eps - (float)kEExc) * G->f_spd2_e);
+        vx = n0 * sp; vy = n1 * sp; vz = n2 * sp;
+        dirty = true;
+        atomicAdd(&sCnt[kCnEExc], 1ull);
+      }
+    } else if (up < F2) {  // ionization (C-10)
+      if (eps >= (float)kEIon) {
+        float a0, a1, a2, c0, c1, c2, g0, g1, g2, g3;
+        iso_dir_f(sc, a0, a1, a2);
+        iso_dir_f(sc, c0, c1, c2);
+        gauss_pair_f(sc, g0, g1);
+        gauss_pair_f(sc, g2, g3);
+        const float sp = sqrtf(0.5f * (eps - (float)kEIon) * G->f_spd2_e);
+        vx = a0 * sp; vy = a1 * sp; vz = a2 * sp;
+        dirty = true;
+        *re = Rec32{cell, off, c0 * sp, c1 * sp, c2 * sp, draw_countdown(next_u(sc), G->f_lnq[0])};
+        *ri = Rec32{cell, off, g0 * G->f_sig_i, g1 * G->f_sig_i, g2 * G->f_sig_i,
+                    draw_countdown(next_u(sc), G->f_lnq[1])};
+        born = 1;
+        deposit32(sCe, cell, off);
+        deposit32(sCi, cell, off);
+        atomicAdd(&sCnt[kCnEIon], 1ull);
+      }
+    }
+  } else {
+    atomicAdd(&sCnt[kCnICand], 1ull);
+    float g0, g1, g2, g3;
+    gauss_pair_f(sc, g0, g1);
+    gauss_pair_f(sc, g2, g3);
+    const float n0 = g0 * G->f_sig_i, n1 = g1 * G->f_sig_i, n2 = g2 * G->f_sig_i;
+    const float gx = vx - n0, gy = vy - n1, gz = vz - n2;
+    const float g2s = gx * gx + gy * gy + gz * gz;
+    float F0, F1, F2;
+    lookup_f(G->fF[1], g2s * G->f_emfac_rel, F0, F1, F2);
+    if (up < F0) {  // isotropic in the centre-of-mass frame
+      float d0, d1, d2;
+      iso_dir_f(sc, d0, d1, d2);
+      const float hg = 0.5f * sqrtf(g2s);
+      vx = 0.5f * (vx + n0) + d0 * hg;
+      vy = 0.5f * (vy + n1) + d1 * hg;
+      vz = 0.5f * (vz + n2) + d2 * hg;
+      dirty = true;
+      atomicAdd(&sCnt[kCnIIso], 1ull);
+    } else if (up < F1) {  // charge transfer
+      vx = n0; vy = n1; vz = n2;
+      dirty = true;
+      atomicAdd(&sCnt[kCnICx], 1ull);
+    }
+  }
+  if (dirty) {
+    G->fvy[S][p] = vy;
+    G->fvz[S][p] = vz;
+  }
+  return CollOut{vx, cd_next, born};
+}
+
+// EEPF sample of an electron in the centre window (reading C-18).
+__device__ __noinline__ void eepf32(const DevCtx* __restrict__ G, long long p, int cell,
+                                    float off, float vx, unsigned long long* sCnt) {
+  const float d = ((float)cell - 0.5f * (float)G->nc) + off;
+  if (!(d > -0.5f && d < 0.5f)) return;
+  const float vy = G->fvy[0][p], vz = G->fvz[0][p];
+  const float eps = (vx * vx + vy * vy + vz * vz) * G->f_emfac_e;
+  if (eps * G->f_eepf_inv_de < (float)G->eepf_bins)
+    atomicAdd(&G->eepf[(int)(eps * G->f_eepf_inv_de)], 1ull);
+  atomicAdd(&sCnt[kCnEepfN], 1ull);
+  atomicAdd(&sCnt[kCnEepfEsum], (unsigned long long)__float2ll_rn(eps * 1048576.0f));
+}
+
+__device__ __forceinline__ void put_rec(float* list, size_t cap, long long slot, const Rec32& r) {
+  list[slot] = __int_as_float(r.cell);
+  list[slot + cap] = r.off;
+  list[slot + 2 * cap] = r.vx;
+  list[slot + 3 * cap] = r.vy;
+  list[slot + 4 * cap] = r.vz;
+  list[slot + 5 * cap] = __int_as_float((int)r.cd);
+}
+
+// A warp's staging of one 128-particle tile (bulk-copy destination; 16-byte aligned fields).
+constexpr int kStages = 3;
+struct WarpTile {
+  unsigned short cell[128], cd[128];
+  float off[128], vx[128];
+  unsigned id[128];
+};
+struct __align__(128) WarpPipe {  // one per warp, back to back in shared memory
+  WarpTile t[kStages];
+  unsigned long long bar[kStages];
+  Rec32 recE[32], recI[32];  // each lane's births of the current particle
+};
+struct PipeCount {           // per-warp, warp-uniform, in registers
+  long long issued, waited;  // tiles issued / consumed by this warp so far
+};
+
+__device__ __forceinline__ unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
+
+// Lane 0 starts the bulk copies of particles [t0, t0 + n) into the next stage.
+template <int S>
+__device__ __forceinline__ void issue_tile(const DevCtx& K, WarpPipe& P, PipeCount& Q,
+                                           long long t0, int n) {
+  if ((threadIdx.x & 31) == 0) {
+    const int st = (int)(Q.issued % kStages);
+    WarpTile& T = P.t[st];
+    const unsigned bh = round16(2u * n), bf = round16(4u * n);
+    fence_proxy_async_smem();  // the lanes' earlier reads of this stage come first
+    mbar_arrive_expect_tx(&P.bar[st], 2u * bh + 3u * bf);
+    bulk_g2s(T.cell, K.cell[S] + t0, bh, &P.bar[st]);
+    bulk_g2s(T.cd, K.cdown[S] + t0, bh, &P.bar[st]);
+    bulk_g2s(T.off, K.off[S] + t0, bf, &P.bar[st]);
+    bulk_g2s(T.vx, K.fvx[S] + t0, bf, &P.bar[st]);
+    bulk_g2s(T.id, K.id[S] + t0, bf, &P.bar[st]);
+  }
+  ++Q.issued;
+}
+
+// One warp walks particles [q, qe) of species S (q a multiple of 32) in 128-particle tiles,
+// kStages - 1 tiles in flight.  Holes and births go to the warp's lists at hk / ek / ik
+// (running offsets, warp-uniform).  Returns false if a staged tile never arrived.
+template <int S>
+__device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long long q,
+                                            long long qe, const float2* sE, unsigned* sCe,
+                                            unsigned* sCi, unsigned long long* sCnt,
+                                            WarpPipe& P, PipeCount& Q, long long& hk,
+                                            long long& ek, long long& ik) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nc = K.nc;
+  const size_t cap = (size_t)K.nchunk_max * kChunk;
+  const DevCtx* __restrict__ G = K.self;
+  const long long ntiles = (qe - q + 127) / 128;
+  for (long long t = 0; t < kStages - 1 && t < ntiles; ++t)
+    issue_tile<S>(K, P, Q, q + 128 * t, (int)min(128ll, qe - q - 128 * t));
+  for (long long t = 0; t < ntiles; ++t) {
+    if (t + kStages - 1 < ntiles) {
+      const long long u = t + kStages - 1;
+      issue_tile<S>(K, P, Q, q + 128 * u, (int)min(128ll, qe - q - 128 * u));
+    }
+    const int st = (int)(Q.waited % kStages);
+    if (!mbar_wait(&P.bar[st], (unsigned)((Q.waited / kStages) & 1))) {
+      atomicOr(&K.st->status, kStTimeout);
+      for (long long w = Q.waited + 1; w < Q.issued; ++w)  // let the copies in flight land
+        (void)mbar_wait(&P.bar[w % kStages], (unsigned)((w / kStages) & 1));
+      Q.waited = Q.issued;
+      return false;
+    }
+    ++Q.waited;
+    const WarpTile& T = P.t[st];
+    const long long tile = q + 128 * t;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      const int ix = 32 * k + lane;
+      const long long p = tile + ix;
+      bool dead = false, be = false, bi = false;
+      if (p < qe) {
+        int cell = T.cell[ix];
+        float off = T.off[ix];
+        float vx = T.vx[ix];
+        unsigned cd = T.cd[ix];
+        // steps 3-4: gather (linear) and leapfrog in cell units
+        const float2 e = sE[cell];
+        vx += e.x + off * e.y;
+        off += vx;
+        renorm(cell, off);
+        if (!isfinite(vx)) atomicOr(&K.st->status, kStNonfinite);
+        const bool out_l = cell < 0 || (cell == 0 && off == 0.0f);
+        if (out_l || cell >= nc) {
+          const SurfOut r = surface32<S>(G, step, p, T.id[ix], cell, off, vx, out_l, sCe, sCnt,
+                                         &P.recE[lane]);
+          cell = r.cell;
+          off = r.off;
+          vx = r.vx;
+          dead = r.flags & 1;
+          be = (r.flags >> 1) & 1;
+        }
+        if (!dead) {
+          // step 6: the countdown to the next null-collision candidate
+          --cd;
+          if ((cd & 0x7FFFu) == 0u) {
+            const CollOut c = collide32<S>(G, step, p, T.id[ix], cell, off, vx, cd, sCe, sCi,
+                                           sCnt, &P.recE[lane], &P.recI[lane]);
+            vx = c.vx;
+            cd = c.cd;
+            bi = c.born != 0;
+            if (S == 0) be = bi;  // an ionization pair
+          }
+          deposit32(S == 0 ? sCe : sCi, cell, off);
+          if (S == 0 && cell >= K.eepf_jlo && cell <= K.eepf_jhi) eepf32(G, p, cell, off, vx, sCnt);
+        }
+        K.cell[S][p] = (unsigned short)cell;
+        K.off[S][p] = off;
+        K.fvx[S][p] = vx;
+        K.cdown[S][p] = (unsigned short)cd;
+      }
+      // particle order within the warp tile is (k, lane): rank by ballot
+      if (__any_sync(0xffffffffu, dead || be || (S == 0 && bi))) {
+        const unsigned mh = __ballot_sync(0xffffffffu, dead);
+        const unsigned me = __ballot_sync(0xffffffffu, be);
+        const unsigned mi = __ballot_sync(0xffffffffu, S == 0 && bi);
+        if (dead) K.hole_idx[S][hk + __popc(mh & lt)] = (int)p;
+        if (be) put_rec(K.feb[S], cap, ek + __popc(me & lt), P.recE[lane]);
+        if (S == 0 && bi) put_rec(K.fib, cap, ik + __popc(mi & lt), P.recI[lane]);
+        hk += __popc(mh);
+        ek += __popc(me);
+        ik += __popc(mi);
+      }
+    }
+    __syncwarp();  // every lane is done with this stage before it is refilled
+  }
+  return true;
+}
+
+__device__ __forceinline__ void flush32(const DevCtx& K, unsigned* sC, unsigned long long* Cn) {
+  __syncthreads();
+  for (int j = threadIdx.x; j < 2 * K.nx; j += blockDim.x) {
+    const unsigned v = sC[j];
+    if (v) {
+      atomicAdd(&Cn[j], (unsigned long long)v << 16);
+      sC[j] = 0u;
+    }
+  }
+  __syncthreads();
+}
+
+// Species S for the whole block: each warp its own range, in rounds that bound the 32-bit
+// counters.
+template <int S>
+__device__ __forceinline__ void block_pass32(const DevCtx& K, unsigned step, long long n,
+                                             const float2* sE, unsigned* sC,
+                                             unsigned long long* sCnt, unsigned long long* Cn,
+                                             WarpPipe& P, PipeCount& Q) {
+  const int GW = K.nlist;  // warps of the grid
+  const int gw = blockIdx.x * kWarps32 + (threadIdx.x >> 5);
+  const long long q0 = range_begin(n, gw, GW), q1 = range_begin(n, gw + 1, GW);
+  long long hk = q0, ek = q0, ik = q0;  // list slots of this warp
+  // rounds: uniform across the block (the widest warp range of the block decides)
+  long long wmax = 0;
+  for (int w = 0; w < kWarps32; ++w) {
+    const int g = blockIdx.x * kWarps32 + w;
+    wmax = max(wmax, range_begin(n, g + 1, GW) - range_begin(n, g, GW));
+  }
+  const int rounds = (int)((wmax + kRoundPerWarp - 1) / kRoundPerWarp);
+  bool ok = true;
+  for (int r = 0; r < rounds; ++r) {
+    const long long a = q0 + (long long)r * kRoundPerWarp;
+    const long long e = min(q1, a + kRoundPerWarp);
+    if (ok && a < e)
+      ok = warp_pass32<S>(K, step, a, e, sE, sC, sC + K.nx, sCnt, P, Q, hk, ek, ik);
+    if (r + 1 < rounds) flush32(K, sC, Cn);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    K.hole_cnt[S][gw] = (int)(hk - q0);
+    K.eb_cnt[S][gw] = (int)(ek - q0);
+    if (S == 0) K.ib_cnt[gw] = (int)(ik - q0);
+  }
+}
+
+__host__ __device__ __forceinline__ size_t pipes_offset(int nx) {
+  return ((sizeof(float2) * 2 * (size_t)nx + sizeof(unsigned) * 2 * (size_t)nx) + 127) &
+         ~size_t(127);
+}
+
+__global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCtx K) {
+  extern __shared__ __align__(128) unsigned char smem32[];
+  const int nx = K.nx;
+  float2* sE = reinterpret_cast<float2*>(smem32);           // [2][nx] kick, kick difference
+  unsigned* sC = reinterpret_cast<unsigned*>(sE + 2 * nx);  // [2][nx] 32-bit counts
+  WarpPipe& P = reinterpret_cast<WarpPipe*>(smem32 + pipes_offset(nx))[threadIdx.x >> 5];
+  __shared__ unsigned long long sCnt[kNumCounters];
+  __shared__ bool sLast;
+  if ((threadIdx.x & 31) == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&P.bar[s], 1u);
+    fence_mbar_init();
+  }
+  PipeCount Q{0, 0};
+  for (int s = 0; s < 2; ++s)
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+      const float a = K.fE[s][j];
+      const float b = (j + 1 < nx) ? K.fE[s][j + 1] : a;
+      sE[s * nx + j] = make_float2(a, b - a);
+    }
+  for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0u;
+  if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
+  const unsigned step = K.st->step;
+  const long long ne = K.st->n[0], ni = K.st->n[1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) K.st->step_next = step + 1;
+  __syncthreads();
+  unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
+  block_pass32<0>(K, step, ne, sE, sC, sCnt, Cn, P, Q);
+  flush32(K, sC, Cn);
+  block_pass32<1>(K, step, ni, sE + nx, sC, sCnt, Cn, P, Q);
+  flush32(K, sC, Cn);
+  if (threadIdx.x < kNumCounters && sCnt[threadIdx.x])
+    atomicAdd(&K.counters[threadIdx.x], sCnt[threadIdx.x]);
+  __threadfence();
+  if (threadIdx.x == 0) sLast = (atomicAdd(&K.st->done_blocks, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (sLast) {
+    __threadfence();
+    // the warps' staging buffers are idle: their shared memory is the scratch
+    finalize_compaction<kBlock / 32>(K, ne, ni, reinterpret_cast<int*>(&P - (threadIdx.x >> 5)),
+                                     (int)(sizeof(WarpPipe) * kWarps32 / sizeof(int)));
+  }
+}
+
+// Record moves of the FP32 representation for the placement launch.
+struct Fp32Moves {
+  static __device__ __forceinline__ void birth(const DevCtx& K, int s, int list, long long slot,
+                                               long long d, unsigned id) {
+    const float* rec = list == 0 ? K.feb[0] : (list == 1 ? K.feb[1] : K.fib);
+    const size_t cap = (size_t)K.nchunk_max * kChunk;
+    K.cell[s][d] = (unsigned short)__float_as_int(rec[slot]);
+    K.off[s][d] = rec[slot + cap];
+    K.fvx[s][d] = rec[slot + 2 * cap];
+    K.fvy[s][d] = rec[slot + 3 * cap];
+    K.fvz[s][d] = rec[slot + 4 * cap];
+    K.cdown[s][d] = (unsigned short)__float_as_int(rec[slot + 5 * cap]);
+    K.id[s][d] = id;
+  }
+  static __device__ __forceinline__ void move(const DevCtx& K, int s, long long t, long long d) {
+    K.cell[s][d] = K.cell[s][t];
+    K.off[s][d] = K.off[s][t];
+    K.fvx[s][d] = K.fvx[s][t];
+    K.fvy[s][d] = K.fvy[s][t];
+    K.fvz[s][d] = K.fvz[s][t];
+    K.cdown[s][d] = K.cdown[s][t];
+    K.id[s][d] = K.id[s][t];
+  }
+};
+
+// FP64 SI state (x, v) -> FP32 cell units, for the initial load and pic_set_particles; draws
+// each particle's countdown from its own stream at the current step.
+__global__ void k_to_fp32(DevCtx K, int s, long long n) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double xn = K.x[s][q] * K.inv_dx;
+  long long j = __double2ll_rd(xn);
+  if (j > K.nc - 1) j = K.nc - 1;
+  if (j < 0) j = 0;
+  K.cell[s][q] = (unsigned short)j;
+  K.off[s][q] = (float)(xn - (double)j);
+  const double sc = K.dt * K.inv_dx;  // m/s -> cells per step
+  K.fvx[s][q] = (float)(K.vx[s][q] * sc);
+  K.fvy[s][q] = (float)(K.vy[s][q] * sc);
+  K.fvz[s][q] = (float)(K.vz[s][q] * sc);
+  Stream st(K, s, kPurCount, K.id[s][q], K.st->step);
+  K.cdown[s][q] = draw_countdown(next_u(st), K.f_lnq[s]);
+}
+
+// FP32 cell units -> FP64 SI state, for pic_get_particles and the diagnostics.
+__global__ void k_to_fp64(DevCtx K, int s, long long n) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  K.x[s][q] = ((double)K.cell[s][q] + (double)K.off[s][q]) * K.dx;
+  K.vx[s][q] = (double)K.fvx[s][q] * K.to_si_v;
+  K.vy[s][q] = (double)K.fvy[s][q] * K.to_si_v;
+  K.vz[s][q] = (double)K.fvz[s][q] * K.to_si_v;
+}
+
+// Deposit of the FP32 state with the FP32 rule (16-bit weights), after a load or a set.
+__global__ void k_deposit32(DevCtx K, int s, int buf, long long n) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int j = K.cell[s][q];
+  const int wr = __float2int_rn(K.off[s][q] * 65536.0f);
+  unsigned long long* C = K.C + (size_t)(buf * 2 + s) * K.nx;
+  atomicAdd(&C[j], (unsigned long long)(65536 - wr) << 16);
+  atomicAdd(&C[j + 1], (unsigned long long)wr << 16);
+}
+
+// ------------------------------------------------------------------------ launchers
+size_t push32_smem_bytes(int nx) { return pipes_offset(nx) + sizeof(WarpPipe) * kWarps32; }
+
+cudaError_t launch_push_fp32(const DevCtx& K, int grid, cudaStream_t s) {
+  k_push_fp32<<<grid, kBlock, push32_smem_bytes(K.nx), s>>>(K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_place_fp32(const DevCtx& K, int grid, cudaStream_t s) {
+  k_place_field<Fp32Moves><<<grid, 256, sizeof(__int128) * (size_t)K.nx, s>>>(K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const DevCtx& K, int species, long long n, bool to_fp32,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  if (to_fp32)
+    k_to_fp32<<<g, 256, 0, s>>>(K, species, n);
+  else
+    k_to_fp64<<<g, 256, 0, s>>>(K, species, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deposit32(const DevCtx& K, int species, int buf, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_deposit32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(K, species, buf, n);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_kernels32(int nx) {
+  cudaError_t e = cudaFuncSetAttribute(k_push_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)push32_smem_bytes(nx));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_place_field<Fp32Moves>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(__int128) * (size_t)nx));
+}
+
+int push_fp32_blocks_per_sm(int nx) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_fp32, kBlock,
+                                                    push32_smem_bytes(nx)) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+}  // namespace pic

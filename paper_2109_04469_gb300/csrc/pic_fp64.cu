@@ -445,7 +445,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_push_fp64(DevCtx K) {
   __syncthreads();
   if (sLast) {
     __threadfence();
-    finalize_compaction<kBlock / 32>(K, ne, ni);
+    // the block's count grids are flushed: their shared memory is the scratch
+    finalize_compaction<kBlock / 32>(K, ne, ni, reinterpret_cast<int*>(sC), 4 * nx);
   }
 }
 

@@ -25,4 +25,14 @@ int push_fp64_blocks_per_sm(int nx);
 // raise the dynamic shared-memory limit of the grid-sized kernels for nx nodes
 cudaError_t configure_kernels(int nx);
 
+// FP32 particle path (pic_fp32.cu)
+cudaError_t launch_push_fp32(const DevCtx& K, int grid, cudaStream_t s);
+cudaError_t launch_place_fp32(const DevCtx& K, int grid, cudaStream_t s);
+// FP64 SI arrays <-> FP32 cell-unit state of one species (n particles)
+cudaError_t launch_convert(const DevCtx& K, int species, long long n, bool to_fp32,
+                           cudaStream_t s);
+cudaError_t launch_deposit32(const DevCtx& K, int species, int buf, long long n, cudaStream_t s);
+cudaError_t configure_kernels32(int nx);
+int push_fp32_blocks_per_sm(int nx);
+
 }  // namespace pic

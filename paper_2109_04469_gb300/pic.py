@@ -23,7 +23,7 @@ N_COUNTERS = 16
 XS_NODES = 100001
 ERRORS = {
     -1: "PIC_ERR_PARAM", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_CAPACITY", -4: "PIC_ERR_NONFINITE",
-    -5: "PIC_ERR_WORKSPACE", 1: "PIC_WARN_UNSTABLE",
+    -5: "PIC_ERR_WORKSPACE", -6: "PIC_ERR_TIMEOUT", 1: "PIC_WARN_UNSTABLE",
 }
 
 

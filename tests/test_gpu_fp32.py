@@ -1,0 +1,140 @@
+"""GPU FP32 particle path (cell index + FP32 offset, FP64 field) against the FP64 oracle.
+
+The FP32 path is not bit-identical to the oracle; its bar is:
+  * the initial state is the FP64 load rounded (one sample for both precisions);
+  * charge conservation, ids and population bookkeeping are exact;
+  * with a negligible self-field (no chaos) trajectories follow the FP64 oracle to FP32
+    rounding, with the same surface decisions;
+  * RF-averaged densities, the centre EEPF mean energy and the ion flux agree with the
+    oracle within 3 combined standard errors over independent seeds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2109_04469_gb300 import pic, workloads
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2109_04469_gb300 import build as B
+
+    B.build()
+    O.build()
+    assert torch.cuda.is_available()
+
+
+def _cfg(**kw):
+    c = workloads.params("ccp_5pa_150v_128c", **kw)
+    c["precision"] = pic.PIC_FP32
+    return c
+
+
+def test_fp32_initial_state_is_the_fp64_load_rounded():
+    cfg = _cfg()
+    sim, ref = pic.Simulation(cfg), O.OracleSim(cfg)
+    dx = cfg["gap_m"] / cfg["n_cells"]
+    for s in (0, 1):
+        g, r = sim.particles(s), ref.particles(s)
+        assert np.array_equal(g["id"], r["id"])
+        assert np.max(np.abs(g["x"] - r["x"])) <= dx * 2.0**-22
+        for k in ("vx", "vy", "vz"):
+            assert np.max(np.abs(g[k] - r[k]) / (np.abs(r[k]) + 1e-30)) <= 2e-7
+    # 16-bit weights times 2^16: the counts hold exactly 2^32 per particle
+    gg = sim.grid()
+    assert int(gg["Ce"].sum()) == 10_000 * 2**32 and int(gg["Ci"].sum()) == 10_000 * 2**32
+    sim.close()
+
+
+def test_fp32_bookkeeping_exact():
+    cfg = _cfg(refl_e=0.3, gamma_see=0.2)
+    sim = pic.Simulation(cfg)
+    for _ in range(5):
+        sim.step(60)
+        assert sim.sync() == 0
+        g = sim.grid()
+        ne, ni = sim.counts()
+        assert int(g["Ce"].sum()) == ne * 2**32 and int(g["Ci"].sum()) == ni * 2**32
+        for s in (0, 1):
+            p = sim.particles(s)
+            assert len(np.unique(p["id"])) == len(p["id"])
+            assert np.all((p["x"] >= 0) & (p["x"] <= cfg["gap_m"]))
+    c = sim.accum()["counters"].astype(np.int64)
+    _, nid_e, nid_i = sim.step_state()
+    assert nid_e == 10_000 + c[8] + c[5] and nid_i == 10_000 + c[8]
+    ne, ni = sim.counts()
+    assert ne == 10_000 + c[8] + c[5] - c[0] - c[1]
+    assert ni == 10_000 + c[8] - c[2] - c[3]
+    sim.close()
+
+
+def test_fp32_vacuum_trajectories_follow_fp64():
+    """Tiny weight (negligible self-field) and no gas: the motion is the RF vacuum field's, so
+    FP32 and the FP64 oracle differ by rounding only; surface decisions use the same draws."""
+    cfg = _cfg(weight=1e-3, pressure_pa=0.0, refl_e=0.5, gamma_see=0.5, init_te_ev=20.0)
+    sim, ref = pic.Simulation(cfg), O.OracleSim(cfg)
+    sim.step(150)
+    ref.step(150)
+    L = cfg["gap_m"]
+    cg, cr = sim.accum()["counters"], ref.accum()["counters"]
+    for k in (0, 1, 2, 3, 4, 5):  # absorbed, reflected, emitted: identical decisions
+        assert cg[k] == cr[k], (k, cg[k], cr[k])
+    for s in (0, 1):
+        g, r = sim.particles(s), ref.particles(s)
+        assert np.array_equal(g["id"], r["id"])
+        orig = r["id"] < 10_000  # emitted electrons start with other (FP32-sampled) directions
+        assert np.max(np.abs(g["x"][orig] - r["x"][orig])) <= 1e-5 * L
+        vs = np.max(np.abs(r["vx"][orig]))
+        assert np.max(np.abs(g["vx"][orig] - r["vx"][orig])) <= 1e-5 * vs
+    sim.close()
+
+
+def _averages(run, cfg, steps, avg_from):
+    run.step(avg_from)
+    run.reset_averages()
+    run.step(steps - avg_from)
+    d = run.diag()
+    L = cfg["gap_m"]
+    x = np.linspace(0, L, cfg["n_cells"] + 1)
+    trap = lambda y: float(np.sum((y[1:] + y[:-1]) * 0.5 * np.diff(x)))
+    return dict(ne=trap(d["n_e"]) / L, ni=trap(d["n_i"]) / L, flux=d["ion_flux"],
+                te=d["te_center_ev"])
+
+
+def test_fp32_statistics_match_oracle():
+    """RF-period averages over 8 independent seeds: FP32 GPU and the FP64 oracle agree within
+    3 combined standard errors (the two use different rounding, so runs decorrelate)."""
+    steps, avg_from, seeds = 2000, 1000, 8
+    res = {"gpu": [], "ref": []}
+    for seed in range(seeds):
+        cfg = _cfg(seed=101 + seed, init_per_species=5000, capacity_per_species=32768)
+        sim = pic.Simulation(cfg)
+        res["gpu"].append(_averages(sim, cfg, steps, avg_from))
+        sim.close()
+        ref = O.OracleSim(cfg)
+        res["ref"].append(_averages(ref, cfg, steps, avg_from))
+    for k in ("ne", "ni", "flux", "te"):
+        a = np.array([r[k] for r in res["gpu"]])
+        b = np.array([r[k] for r in res["ref"]])
+        se = math.sqrt(a.var(ddof=1) / seeds + b.var(ddof=1) / seeds)
+        print(k, a.mean(), b.mean(), se)
+        assert abs(a.mean() - b.mean()) <= 3 * se + 1e-12 * abs(b.mean()), (k, a.mean(), b.mean(), se)
+
+
+def test_fp32_full_size_workload_runs():
+    """The production workload in FP32: bookkeeping stays exact over a few steps."""
+    cfg = workloads.params("ccp_1pa_300v_400c")
+    cfg["precision"] = pic.PIC_FP32
+    sim = pic.Simulation(cfg)
+    sim.step(5)
+    assert sim.sync() == 0
+    ne, ni = sim.counts()
+    g = sim.grid()
+    assert int(g["Ce"].sum()) == ne * 2**32 and int(g["Ci"].sum()) == ni * 2**32
+    assert 1.9e6 < ne < 2.1e6 and 1.9e6 < ni < 2.1e6
+    sim.close()
