@@ -31,6 +31,7 @@ extern "C" {
 #define PIC_ERR_NONFINITE (-4)  /* a velocity became NaN or infinite */
 #define PIC_ERR_WORKSPACE (-5)  /* workspace missing, too small or misaligned */
 #define PIC_ERR_TIMEOUT (-6)    /* a bounded device wait ran out; results of the step invalid */
+#define PIC_ERR_SCRATCH (-7)    /* n_cells above PIC_FIELD_STATIC_MAX_CELLS (pic_field_solve_static) */
 #define PIC_WARN_UNSTABLE 1     /* omega_pe*dt > 2: the leapfrog stability bound of §3.5 */
 
 #define PIC_FP64 0 /* FP64 particle state; bit-for-bit the oracle's step contract */
@@ -175,6 +176,46 @@ void pic_free(pic_handle* h);
 
 /* Static string for a return code. */
 const char* pic_strerror(int code);
+
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free field solve.  The paper has no counterpart: it is a deployment variant of
+ * the field solve of §2 step 2 (exact discrete Green's function, reading C-23) for callers
+ * that cannot allocate device memory -- code recorded into a CUDA graph by stream capture,
+ * processes whose caching allocator owns the whole device, or library users with no
+ * workspace to hand over.  It uses no handle, no workspace and no allocating call (CUDA or
+ * otherwise): its one scratch array, the int128 sums S_j (16 bytes per node), is a
+ * file-scope device array of PIC_FIELD_STATIC_MAX_CELLS + 1 nodes (1 MiB) inside libpic.so.
+ *
+ * charge_e, charge_i  DEVICE int64 arrays [n_cells + 1], the charge counts at the nodes in
+ *                     units of 2^-32 superparticles (the layout pic_get_grid returns).
+ * n_cells             N, 2 <= N <= PIC_FIELD_STATIC_MAX_CELLS.
+ * gap_m, weight, area_m2, v_left
+ *                     electrode gap L, superparticle weight W, electrode area A, and the
+ *                     potential of the driven electrode at x = 0 (the one at x = L is 0 V).
+ * phi, efield         DEVICE double arrays [n_cells + 1] written by the call (caller-owned).
+ * cuda_stream         cudaStream_t to enqueue on (NULL: legacy default stream).
+ *
+ * All four arrays must be device (or managed) memory of the current device, 8-byte aligned,
+ * and must not overlap each other.  For the same counts and voltage the result is bit for
+ * bit that of pic_solve_field / pic_get_grid of a handle with the same gap, weight, area and
+ * n_cells.  Nothing has to be zeroed beforehand: every scratch element read is written
+ * earlier in the same launch.
+ *
+ * Returns PIC_ERR_SCRATCH for n_cells > PIC_FIELD_STATIC_MAX_CELLS (nothing is launched),
+ * PIC_ERR_PARAM for other invalid arguments (non-device or misaligned pointer, N < 2,
+ * non-positive or non-finite sizes), PIC_ERR_CUDA if the set-up or the launch fails.
+ * Enqueued only: the results are ready when the stream reaches them.
+ *
+ * Set-up: the first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call outside stream capture.
+ * Concurrency: all calls on one device share the scratch array, so two calls whose launches
+ * can run at the same time (different streams, or parallel branches of one graph) race and
+ * give wrong results.  Order them on one stream or with events.
+ * --------------------------------------------------------------------------------------- */
+#define PIC_FIELD_STATIC_MAX_CELLS 65536
+int pic_field_solve_static(const int64_t* charge_e, const int64_t* charge_i, int32_t n_cells,
+                           double gap_m, double weight, double area_m2, double v_left,
+                           double* phi, double* efield, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,8 @@ UNITS = {
     # statistical FP32 path: contraction allowed (its FP64 field solve uses explicit
     # round-to-nearest intrinsics)
     "pic_fp32.cu": [],
+    # allocation-free field solve: same rounded FP64 operations as the FP64 path
+    "pic_static.cu": ["-fmad=false"],
 }
 
 

@@ -770,6 +770,8 @@ const char* pic_strerror(int code) {
     case PIC_ERR_NONFINITE: return "non-finite particle velocity";
     case PIC_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
     case PIC_ERR_TIMEOUT: return "a bounded device wait ran out (staged data never arrived)";
+    case PIC_ERR_SCRATCH:
+      return "n_cells above PIC_FIELD_STATIC_MAX_CELLS, the static scratch of pic_field_solve_static";
     case PIC_WARN_UNSTABLE: return "omega_pe*dt above the leapfrog stability bound 2";
     default: return "unknown code";
   }

@@ -23,7 +23,8 @@ N_COUNTERS = 16
 XS_NODES = 100001
 ERRORS = {
     -1: "PIC_ERR_PARAM", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_CAPACITY", -4: "PIC_ERR_NONFINITE",
-    -5: "PIC_ERR_WORKSPACE", -6: "PIC_ERR_TIMEOUT", 1: "PIC_WARN_UNSTABLE",
+    -5: "PIC_ERR_WORKSPACE", -6: "PIC_ERR_TIMEOUT", -7: "PIC_ERR_SCRATCH",
+    1: "PIC_WARN_UNSTABLE",
 }
 
 
@@ -99,6 +100,8 @@ def lib() -> C.CDLL:
                 "pic_get_derived": (C.c_int, [P, P]),
                 "pic_free": (None, [P]),
                 "pic_strerror": (C.c_char_p, [C.c_int]),
+                "pic_field_solve_static": (C.c_int, [P, P, C.c_int32, C.c_double, C.c_double,
+                                                     C.c_double, C.c_double, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -279,3 +282,27 @@ class Simulation:
             out[name] = np.array(v[:], dtype=np.uint64) if name == "counters" else v
         out["return_code"] = rc
         return out
+
+
+FIELD_STATIC_MAX_CELLS = 65536
+
+
+def field_solve_static(charge_e, charge_i, n_cells: int, gap_m: float, weight: float,
+                       area_m2: float, v_left: float, phi, efield, stream=None) -> int:
+    """pic_field_solve_static on CUDA tensors: int64 charge counts [n_cells + 1] in, float64
+    phi and E [n_cells + 1] out, enqueued on `stream` (default: torch's current stream).
+    Allocates no device memory; calls that may run at the same time on one device race on
+    the library's static scratch array.  Returns the C-ABI code, raising on errors."""
+    import torch
+
+    for t, dt in ((charge_e, torch.int64), (charge_i, torch.int64), (phi, torch.float64),
+                  (efield, torch.float64)):
+        if t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() < n_cells + 1:
+            raise ValueError("field_solve_static: contiguous CUDA tensors of n_cells + 1 "
+                             "int64 (charges) and float64 (phi, efield) elements expected")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _check(lib().pic_field_solve_static(
+        C.c_void_p(charge_e.data_ptr()), C.c_void_p(charge_i.data_ptr()), int(n_cells),
+        float(gap_m), float(weight), float(area_m2), float(v_left),
+        C.c_void_p(phi.data_ptr()), C.c_void_p(efield.data_ptr()), C.c_void_p(s.cuda_stream)),
+        "pic_field_solve_static")
