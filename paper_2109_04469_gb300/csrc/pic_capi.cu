@@ -156,6 +156,16 @@ struct Carver {
 // (FP32 handles keep one list per warp: 8 per block of at most capacity/256 blocks.)
 long long max_list_blocks(const pic_params& p) { return p.capacity_per_species / 32 + 8192; }
 
+// Count arrays of the lists (reading C-15) at stride G inside their block:
+// holes e, holes i, electron births from e / i ranges, ion births.
+void set_list_counts(DevCtx& K, int G) {
+  int* base = K.hole_cnt[0];
+  K.hole_cnt[1] = base + G;
+  K.eb_cnt[0] = base + 2 * (size_t)G;
+  K.eb_cnt[1] = base + 3 * (size_t)G;
+  K.ib_cnt = base + 4 * (size_t)G;
+}
+
 void carve(const pic_params& p, char* base, DevCtx& K, size_t* total) {
   Carver c{base};
   const int nx = p.n_cells + 1;
@@ -185,16 +195,15 @@ void carve(const pic_params& p, char* base, DevCtx& K, size_t* total) {
   // per-block list counts: the particle grid has at most max_list_blocks(p) blocks
   const size_t nl = (size_t)max_list_blocks(p);
   const bool fp32 = p.precision == PIC_FP32;
+  // the five count arrays are one contiguous block (placed with stride nlist by
+  // set_list_counts once the grid is known), so the placement launch stages them with
+  // 16-byte loads; 4 ints of padding for the last rounded load
+  K.hole_cnt[0] = c.take<int>(5 * nl + 4);
+  set_list_counts(K, (int)nl);
   for (int s = 0; s < 2; ++s) {
     K.hole_idx[s] = c.take<int>(cap);
-    K.hole_cnt[s] = c.take<int>(nl);
-    K.hole_pref[s] = c.take<int>(nl);
-    K.eb_cnt[s] = c.take<int>(nl);
-    K.eb_pref[s] = c.take<int>(nl);
     K.eb[s] = fp32 ? nullptr : c.take<double>(4 * cap);
   }
-  K.ib_cnt = c.take<int>(nl);
-  K.ib_pref = c.take<int>(nl);
   K.ib = fp32 ? nullptr : c.take<double>(4 * cap);
   if (fp32) {
     for (int s = 0; s < 2; ++s) {
@@ -401,7 +410,11 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   h->place_grid = 1 + sms;
   // hole / birth list owners: particle blocks (FP64 pass) or their warps (FP32 pass)
   K.nlist = fp32 ? h->push_grid * (kBlock / 32) : h->push_grid;
-  h->K.nlist = K.nlist;
+  set_list_counts(K, K.nlist);
+  h->K = K;
+  if ((fp32 ? configure_place_fp32(nx, K.nlist) : configure_place_fp64(nx, K.nlist)) !=
+      cudaSuccess)
+    return fail(PIC_ERR_CUDA);
 
   DevState s0;
   std::memset(&s0, 0, sizeof s0);

@@ -10,6 +10,33 @@
 
 namespace pic {
 
+// Programmatic dependent launch between the step's two launches (and into the next step):
+// a kernel launched with launch_chained may be scheduled while the previous kernel of the
+// stream still runs, once every block of that kernel has called chain_release();
+// chain_wait() then returns when the previous kernel has completed and its writes are
+// visible.  Nothing written by an earlier kernel may be read before chain_wait().  In a
+// kernel launched the ordinary way both are no-ops.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void chain_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... Args>
+cudaError_t launch_chained(void (*kernel)(Args...), unsigned grid, unsigned block, size_t smem,
+                           cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int NW>
 __device__ __forceinline__ int block_excl_scan(int v, int* sWarp, int& total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -183,6 +210,17 @@ __device__ __forceinline__ void field_solve(const DevCtx& K, unsigned step, int 
   }
 }
 
+// Thread 0 of block 0 of a particle pass: the step index and the counts and id counters the
+// pass starts from, for the placement launch (which publishes new ones).
+__device__ __forceinline__ void snapshot_pass(const DevCtx& K, unsigned step, long long ne,
+                                              long long ni) {
+  K.st->step_next = step + 1;
+  K.st->n_snap[0] = ne;
+  K.st->n_snap[1] = ni;
+  K.st->id_snap[0] = K.st->next_id[0];
+  K.st->id_snap[1] = K.st->next_id[1];
+}
+
 // Block 0 of the placement launch: close step n's accumulation (acc += C(n), counted),
 // clear that buffer for the deposit of step n+1, solve the field of step n+1, advance the
 // step index.
@@ -223,55 +261,81 @@ __device__ __forceinline__ int upper_bound_i(const int* a, int n, long long v) {
   return lo;
 }
 
-__device__ __forceinline__ int lower_bound_i(const int* a, int n, long long v) {
+// Position of v in the ascending list a[0, n) (the number of entries below v) and whether v
+// is in it: binary steps down to 32 entries, then one pass whose loads are all independent.
+__device__ __forceinline__ int find_sorted(const int* a, int n, long long v, bool& found) {
   int lo = 0, hi = n;
-  while (lo < hi) {
+  while (hi - lo > 32) {
     const int mid = (lo + hi) >> 1;
     if ((long long)a[mid] < v)
       lo = mid + 1;
     else
       hi = mid;
   }
-  return lo;
+  int lb = lo;
+  bool f = false;
+#pragma unroll 8
+  for (int i = lo; i < hi; ++i) {
+    const long long x = a[i];
+    lb += x < v ? 1 : 0;
+    f |= x == v;
+  }
+  if (lb == hi && hi < n && !f) f = (long long)a[hi] == v;  // a[hi] >= v after the binary steps
+  found = f;
+  return lb;
 }
 
-// Run by the last particle block to finish (after a fence): exclusive prefixes of the five
-// per-block count arrays in one block scan, the totals of reading C-15 for both species,
-// the new counts and ids.  NW = warps of the block.
-// scratch: free shared memory of the block (scratch_ints ints); when it holds the five count
-// arrays they are first staged there with coalesced loads, so the serial per-thread segments
-// read shared memory instead of waiting on one global load after another.
-template <int NW>
-__device__ void finalize_compaction(const DevCtx& K, long long ne, long long ni, int* scratch,
-                                    int scratch_ints) {
-  constexpr int kA = 5;
+// Shared memory of the placement launch: the Green's-function sums of block 0, or the five
+// prefix arrays of the other blocks.
+__host__ __device__ __forceinline__ size_t place_smem_bytes(int nx, int nlist) {
+  const size_t field = sizeof(__int128) * (size_t)nx;
+  const size_t lists = sizeof(int) * (5 * (size_t)nlist + 4);  // + rounding of 16-B loads
+  return field > lists ? field : lists;
+}
+
+// Reading C-15, run by every placement block into its own shared memory: the exclusive
+// prefixes of the five per-owner count arrays (sp[a * G + c]: a = 0, 1 holes of electrons /
+// ions; 2 electron births from electron ranges; 3 electron births from ion ranges, whose
+// ranks continue those of list 2; 4 ion births) and the totals of both species.  The counts
+// of the particle pass are read once with coalesced loads; nothing waits on another block.
+template <int NT>
+__device__ void list_prefixes(const DevCtx& K, int* sp, CompactTot* sT) {
+  constexpr int kA = 5, NW = NT / 32, kBatch = 12;
   __shared__ int wsum[NW][kA], wtot[kA];
-  __shared__ long long sq[2];
+  __shared__ int sq[2];
   const int G = K.nlist;  // list owners: particle blocks (FP64 pass) or warps (FP32 pass)
-  int* gcnt[kA] = {K.hole_cnt[0], K.hole_cnt[1], K.eb_cnt[0], K.eb_cnt[1], K.ib_cnt};
-  int* pref[kA] = {K.hole_pref[0], K.hole_pref[1], K.eb_pref[0], K.eb_pref[1], K.ib_pref};
-  const int* cnt[kA];
-  if (kA * G <= scratch_ints) {
-    for (int i = threadIdx.x; i < kA * G; i += blockDim.x) scratch[i] = gcnt[i / G][i % G];
-    __syncthreads();
+  const long long N2[2] = {K.st->n_snap[0], K.st->n_snap[1]};  // loads overlap the staging
+  const unsigned nid2[2] = {K.st->id_snap[0], K.st->id_snap[1]};
+  // the five count arrays lie contiguously at stride G from hole_cnt[0] (16-byte aligned,
+  // padded): one pass of 16-byte loads, all in flight together for up to 12 per thread
+  {
+    const int4* src = reinterpret_cast<const int4*>(K.hole_cnt[0]);
+    int4* dst = reinterpret_cast<int4*>(sp);
+    const int n4 = (kA * G + 3) / 4;
+    for (int i0 = threadIdx.x; i0 < n4; i0 += kBatch * NT) {
+      int4 v[kBatch];
 #pragma unroll
-    for (int a = 0; a < kA; ++a) cnt[a] = scratch + a * G;
-  } else {
+      for (int u = 0; u < kBatch; ++u) {
+        const int i = i0 + u * NT;
+        if (i < n4) v[u] = __ldcg(src + i);
+      }
 #pragma unroll
-    for (int a = 0; a < kA; ++a) cnt[a] = gcnt[a];
+      for (int u = 0; u < kBatch; ++u) {
+        const int i = i0 + u * NT;
+        if (i < n4) dst[i] = v[u];
+      }
+    }
   }
-  const int seg = (G + blockDim.x - 1) / blockDim.x;
+  if (threadIdx.x < 2) sq[threadIdx.x] = 0;
+  __syncthreads();
+  const int seg = (G + NT - 1) / NT;
   const int c0 = min((int)threadIdx.x * seg, G), c1 = min(c0 + seg, G);
-  int loc[kA];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int loc[kA], inc[kA];
 #pragma unroll
   for (int a = 0; a < kA; ++a) {
     loc[a] = 0;
-    for (int c = c0; c < c1; ++c) loc[a] += cnt[a][c];
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int inc[kA];
-#pragma unroll
-  for (int a = 0; a < kA; ++a) {
+    for (int c = c0; c < c1; ++c) loc[a] += sp[a * G + c];
     inc[a] = loc[a];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -293,78 +357,89 @@ __device__ void finalize_compaction(const DevCtx& K, long long ne, long long ni,
   __syncthreads();
 #pragma unroll
   for (int a = 0; a < kA; ++a) {
-    // the second electron-birth list continues the ranks of the first
     int run = wsum[w][a] + inc[a] - loc[a] + (a == 3 ? wtot[2] : 0);
     for (int c = c0; c < c1; ++c) {
-      pref[a][c] = run;
-      run += cnt[a][c];
+      const int v = sp[a * G + c];
+      sp[a * G + c] = run;
+      run += v;
     }
   }
-  const int He = wtot[0], Hi = wtot[1], Be0 = wtot[2], Be = wtot[2] + wtot[3], Bi = wtot[4];
-  // holes below Nn (needed when tail survivors fill holes): prefix of the block owning Nn
-  // plus its list entries below Nn, counted by the whole block
-  if (threadIdx.x < 2) sq[threadIdx.x] = 0;
-  __syncthreads();
+  const int H2[2] = {wtot[0], wtot[1]};
+  const int B2[2] = {wtot[2] + wtot[3], wtot[4]};
+  // holes below Nn (needed when tail survivors fill holes): prefix of the owner of Nn plus
+  // its list entries below Nn, counted by the whole block
+  long long Nn2[2], Beff2[2];
+  int owner[2];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    const long long N = s ? ni : ne, H = s ? Hi : He, B = s ? Bi : Be;
-    const long long limit = K.cap - (N - H);
-    const long long Beff = B < limit ? B : limit;
-    const long long Nn = N - H + Beff;
-    if (H > Beff) {
-      const int b = range_owner(N, Nn, G);
-      const int* list = K.hole_idx[s] + list_base(N, b, G);
-      const int m = K.hole_cnt[s][b];
-      int below = 0;
-      for (int r = threadIdx.x; r < m; r += blockDim.x) below += ((long long)list[r] < Nn) ? 1 : 0;
-      if (below) atomicAdd((unsigned long long*)&sq[s], (unsigned long long)below);
+    const long long limit = K.cap - (N2[s] - H2[s]);
+    Beff2[s] = B2[s] < limit ? B2[s] : limit;
+    Nn2[s] = N2[s] - H2[s] + Beff2[s];
+    owner[s] = -1;
+    if (H2[s] > Beff2[s]) {
+      const int b = range_owner(N2[s], Nn2[s], G);
+      owner[s] = b;
+      const int* list = K.hole_idx[s] + list_base(N2[s], b, G);
+      const int m = (b + 1 < G ? sp[s * G + b + 1] : H2[s]) - sp[s * G + b];
+      unsigned below = 0;
+      for (int r = threadIdx.x; r < m; r += NT) below += ((long long)list[r] < Nn2[s]) ? 1u : 0u;
+      below = __reduce_add_sync(0xffffffffu, below);
+      if (lane == 0 && below) atomicAdd(&sq[s], (int)below);
     }
   }
   __syncthreads();
   if (threadIdx.x < 2) {
     const int s = threadIdx.x;
     CompactTot t;
-    t.N = s ? ni : ne;
-    t.H = s ? Hi : He;
-    t.B = s ? Bi : Be;
-    t.B0 = s ? Bi : Be0;
-    const long long limit = K.cap - (t.N - t.H);
-    t.Beff = t.B < limit ? t.B : limit;
-    t.Nn = t.N - t.H + t.Beff;
-    t.q = 0;
-    if (t.H > t.Beff) t.q = K.hole_pref[s][range_owner(t.N, t.Nn, G)] + sq[s];
+    t.N = N2[s];
+    t.H = H2[s];
+    t.B = B2[s];
+    t.B0 = s ? wtot[4] : wtot[2];
+    t.Beff = Beff2[s];
+    t.Nn = Nn2[s];
+    t.q = owner[s] >= 0 ? (long long)sp[s * G + owner[s]] + sq[s] : 0;
+    t.nid = nid2[s];
     t.pad = 0;
-    t.nid = K.st->next_id[s];
-    K.st->tot[s] = t;
-    K.st->n[s] = t.Nn;
-    K.st->next_id[s] = t.nid + (unsigned)t.Beff;
+    sT[s] = t;
+  }
+  __syncthreads();
+}
+
+// Index of the hole of rank r of species s (hp: that species' hole prefixes).
+__device__ __forceinline__ long long hole_of_rank(const DevCtx& K, const int* hp, int s,
+                                                  long long r, const CompactTot& t) {
+  const int b = upper_bound_i(hp, K.nlist, r) - 1;
+  return K.hole_idx[s][list_base(t.N, b, K.nlist) + (r - hp[b])];
+}
+
+// Placement launch: block 0 advances the field; the other blocks each total the lists, then
+// place every birth (into the holes by rank, then after N) and move every tail survivor
+// (index >= Nn, not a hole) into the remaining holes below Nn, in ascending order.  Block 1
+// publishes the new counts and id counters.  P supplies the record moves of the particle
+// representation: P::birth(K, s, list, slot, d, id) and P::move(K, s, t, d).
+template <class P>
+__global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
+  extern __shared__ __align__(16) unsigned char place_smem[];
+  chain_release();  // the next particle pass may take the SM room this launch leaves
+  chain_wait();     // the particle pass of this step has completed
+  if (blockIdx.x == 0) {
+    advance_field(K, place_smem);
+    return;
+  }
+  __shared__ CompactTot sT[2];
+  int* sp = reinterpret_cast<int*>(place_smem);
+  list_prefixes<256>(K, sp, sT);
+  const CompactTot &te = sT[0], &ti = sT[1];  // shared: no per-thread copies
+  if (blockIdx.x == 1 && threadIdx.x < 2) {
+    const CompactTot& t = sT[threadIdx.x];
+    K.st->n[threadIdx.x] = t.Nn;
+    K.st->next_id[threadIdx.x] = t.nid + (unsigned)t.Beff;
     if (t.B > t.Beff) {
       atomicOr(&K.st->status, kStCapacity);
       atomicAdd(&K.counters[kCnDropped], (unsigned long long)(t.B - t.Beff));
     }
   }
-  if (threadIdx.x == 0) K.st->done_blocks = 0u;
-}
-
-// Index of the hole of rank r of species s.
-__device__ __forceinline__ long long hole_of_rank(const DevCtx& K, int s, long long r,
-                                                  const CompactTot& t) {
-  const int b = upper_bound_i(K.hole_pref[s], K.nlist, r) - 1;
-  return K.hole_idx[s][list_base(t.N, b, K.nlist) + (r - K.hole_pref[s][b])];
-}
-
-// Placement launch: block 0 advances the field; the other blocks place every birth (into
-// the holes by rank, then after N) and move every tail survivor (index >= Nn, not a hole)
-// into the remaining holes below Nn, in ascending order.  P supplies the record moves of
-// the particle representation: P::birth(K, s, list, slot, d, id) and P::move(K, s, t, d).
-template <class P>
-__global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
-  extern __shared__ __align__(16) unsigned char place_smem[];
-  if (blockIdx.x == 0) {
-    advance_field(K, place_smem);
-    return;
-  }
-  const CompactTot te = K.st->tot[0], ti = K.st->tot[1];
+  const int G = K.nlist;
   const long long tle = te.H > te.Beff ? te.N - te.Nn : 0;
   const long long tli = ti.H > ti.Beff ? ti.N - ti.Nn : 0;
   const long long n_items = te.Beff + tle + ti.Beff + tli;
@@ -383,38 +458,40 @@ __global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
       v -= ti.Beff;
       s = 1; birth = false;
     }
-    const CompactTot& t = s ? ti : te;
+    const CompactTot& t = sT[s];
+    const int* hp = sp + s * G;
     if (birth) {
       const long long r = v;
       int list, b;
       long long slot;
-      // electron births come from the blocks' electron ranges (ionization) and ion ranges
+      // electron births come from the owners' electron ranges (ionization) and ion ranges
       // (emission); ion births from the electron ranges
       if (s == 0 && r < t.B0) {
         list = 0;
-        b = upper_bound_i(K.eb_pref[0], K.nlist, r) - 1;
-        slot = list_base(te.N, b, K.nlist) + (r - K.eb_pref[0][b]);
+        b = upper_bound_i(sp + 2 * G, G, r) - 1;
+        slot = list_base(te.N, b, G) + (r - sp[2 * G + b]);
       } else if (s == 0) {
         list = 1;
-        b = upper_bound_i(K.eb_pref[1], K.nlist, r) - 1;
-        slot = list_base(ti.N, b, K.nlist) + (r - K.eb_pref[1][b]);
+        b = upper_bound_i(sp + 3 * G, G, r) - 1;
+        slot = list_base(ti.N, b, G) + (r - sp[3 * G + b]);
       } else {
         list = 2;
-        b = upper_bound_i(K.ib_pref, K.nlist, r) - 1;
-        slot = list_base(te.N, b, K.nlist) + (r - K.ib_pref[b]);
+        b = upper_bound_i(sp + 4 * G, G, r) - 1;
+        slot = list_base(te.N, b, G) + (r - sp[4 * G + b]);
       }
-      const long long d = (r < t.H) ? hole_of_rank(K, s, r, t) : t.N + r - t.H;
+      const long long d = (r < t.H) ? hole_of_rank(K, hp, s, r, t) : t.N + r - t.H;
       P::birth(K, s, list, slot, d, t.nid + (unsigned)r);
     } else {
       const long long idx = t.Nn + v;  // a tail position
-      const int b = range_owner(t.N, idx, K.nlist);
-      const int* list = K.hole_idx[s] + list_base(t.N, b, K.nlist);
-      const int m = K.hole_cnt[s][b];
-      const int lb = lower_bound_i(list, m, idx);
-      if (lb < m && list[lb] == idx) continue;  // the tail position is itself a hole
-      const long long before = (long long)K.hole_pref[s][b] + lb;  // holes below idx
-      const long long j = (idx - t.Nn) - (before - t.q);             // rank among survivors
-      P::move(K, s, idx, hole_of_rank(K, s, t.Beff + j, t));
+      const int b = range_owner(t.N, idx, G);
+      const int* list = K.hole_idx[s] + list_base(t.N, b, G);
+      const int m = (b + 1 < G ? hp[b + 1] : (int)t.H) - hp[b];
+      bool is_hole;
+      const int lb = find_sorted(list, m, idx, is_hole);
+      if (is_hole) continue;  // the tail position is itself a hole
+      const long long before = (long long)hp[b] + lb;  // holes below idx
+      const long long j = (idx - t.Nn) - (before - t.q);  // rank among survivors
+      P::move(K, s, idx, hole_of_rank(K, hp, s, t.Beff + j, t));
     }
   }
 }

@@ -72,9 +72,7 @@ struct DevState {
   int status;           // sticky kSt* bits
   long long steps_avg;  // steps added to the RF-average accumulators
   unsigned long long vmax_bits;  // scratch of the |vx| maximum reduction
-  unsigned done_blocks;          // particle blocks finished in the current pass
-  unsigned pad;
-  CompactTot tot[2];
+  unsigned id_snap[2];           // next_id at the start of the current step's particle pass
 };
 
 // Everything a kernel needs, passed by value (constant bank).  Pointers address the
@@ -101,14 +99,15 @@ struct DevCtx {
   const double *inv_den, *vtab, *F[2];
   unsigned long long *eepf, *fedf, *counters;  // fedf [2][fedf_bins]
   DevState *st;
-  // per-step scratch (hole / birth bookkeeping).  Particle block b owns a contiguous range
-  // of chunks; its lists start at the slot of its first chunk of each species and are in
-  // particle order.  Counts and exclusive prefixes are per block ([nlist] entries).
-  int nlist;            // entries of the per-block count arrays (>= the particle grid)
+  // per-step scratch (hole / birth bookkeeping).  List owner b (a particle block of the
+  // FP64 pass, a warp of the FP32 pass) owns a contiguous range of each species; its lists
+  // start at the slot of its first particle and are in particle order.  The counts are per
+  // owner ([nlist] entries); the placement launch forms their prefixes in shared memory.
+  int nlist;            // list owners of the particle pass
   int *hole_idx[2];     // [cap]: hole indices
-  int *hole_cnt[2], *hole_pref[2];
-  int *eb_cnt[2], *eb_pref[2];  // electron births from blocks' species-s chunks
-  int *ib_cnt, *ib_pref;        // ion births from blocks' electron chunks
+  int *hole_cnt[2];
+  int *eb_cnt[2];       // electron births from owners' species-s ranges
+  int *ib_cnt;          // ion births from owners' electron ranges
   double *eb[2];        // [4][cap] records x, vx, vy, vz of electron births (FP64 state)
   double *ib;           // [4][cap] ion births (FP64 state)
   // FP32 particle state (precision PIC_FP32): position = cell + off in cells, off in [0, 1]

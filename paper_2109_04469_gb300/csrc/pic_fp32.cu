@@ -515,23 +515,24 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
   unsigned* sC = reinterpret_cast<unsigned*>(sE + 2 * nx);  // [2][nx] 32-bit counts
   WarpPipe& P = reinterpret_cast<WarpPipe*>(smem32 + pipes_offset(nx))[threadIdx.x >> 5];
   __shared__ unsigned long long sCnt[kNumCounters];
-  __shared__ bool sLast;
+  chain_release();  // the placement launch may take the SM room this pass leaves
   if ((threadIdx.x & 31) == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&P.bar[s], 1u);
     fence_mbar_init();
   }
   PipeCount Q{0, 0};
+  for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0u;
+  if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
+  chain_wait();  // the kick tables and counts of the previous launch are complete
   for (int s = 0; s < 2; ++s)
     for (int j = threadIdx.x; j < nx; j += blockDim.x) {
       const float a = K.fE[s][j];
       const float b = (j + 1 < nx) ? K.fE[s][j + 1] : a;
       sE[s * nx + j] = make_float2(a, b - a);
     }
-  for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0u;
-  if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
   const unsigned step = K.st->step;
   const long long ne = K.st->n[0], ni = K.st->n[1];
-  if (blockIdx.x == 0 && threadIdx.x == 0) K.st->step_next = step + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) snapshot_pass(K, step, ne, ni);
   __syncthreads();
   unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
   block_pass32<0>(K, step, ne, sE, sC, sCnt, Cn, P, Q);
@@ -540,39 +541,36 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
   flush32(K, sC, Cn);
   if (threadIdx.x < kNumCounters && sCnt[threadIdx.x])
     atomicAdd(&K.counters[threadIdx.x], sCnt[threadIdx.x]);
-  __threadfence();
-  if (threadIdx.x == 0) sLast = (atomicAdd(&K.st->done_blocks, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (sLast) {
-    __threadfence();
-    // the warps' staging buffers are idle: their shared memory is the scratch
-    finalize_compaction<kBlock / 32>(K, ne, ni, reinterpret_cast<int*>(&P - (threadIdx.x >> 5)),
-                                     (int)(sizeof(WarpPipe) * kWarps32 / sizeof(int)));
-  }
 }
 
 // Record moves of the FP32 representation for the placement launch.
 struct Fp32Moves {
+  // every field is loaded before the first store, so the loads are in flight together
   static __device__ __forceinline__ void birth(const DevCtx& K, int s, int list, long long slot,
                                                long long d, unsigned id) {
     const float* rec = list == 0 ? K.feb[0] : (list == 1 ? K.feb[1] : K.fib);
     const size_t cap = (size_t)K.nchunk_max * kChunk;
-    K.cell[s][d] = (unsigned short)__float_as_int(rec[slot]);
-    K.off[s][d] = rec[slot + cap];
-    K.fvx[s][d] = rec[slot + 2 * cap];
-    K.fvy[s][d] = rec[slot + 3 * cap];
-    K.fvz[s][d] = rec[slot + 4 * cap];
-    K.cdown[s][d] = (unsigned short)__float_as_int(rec[slot + 5 * cap]);
+    const float c = rec[slot], o = rec[slot + cap], vx = rec[slot + 2 * cap],
+                vy = rec[slot + 3 * cap], vz = rec[slot + 4 * cap], cd = rec[slot + 5 * cap];
+    K.cell[s][d] = (unsigned short)__float_as_int(c);
+    K.off[s][d] = o;
+    K.fvx[s][d] = vx;
+    K.fvy[s][d] = vy;
+    K.fvz[s][d] = vz;
+    K.cdown[s][d] = (unsigned short)__float_as_int(cd);
     K.id[s][d] = id;
   }
   static __device__ __forceinline__ void move(const DevCtx& K, int s, long long t, long long d) {
-    K.cell[s][d] = K.cell[s][t];
-    K.off[s][d] = K.off[s][t];
-    K.fvx[s][d] = K.fvx[s][t];
-    K.fvy[s][d] = K.fvy[s][t];
-    K.fvz[s][d] = K.fvz[s][t];
-    K.cdown[s][d] = K.cdown[s][t];
-    K.id[s][d] = K.id[s][t];
+    const unsigned short c = K.cell[s][t], cd = K.cdown[s][t];
+    const float o = K.off[s][t], vx = K.fvx[s][t], vy = K.fvy[s][t], vz = K.fvz[s][t];
+    const unsigned id = K.id[s][t];
+    K.cell[s][d] = c;
+    K.off[s][d] = o;
+    K.fvx[s][d] = vx;
+    K.fvy[s][d] = vy;
+    K.fvz[s][d] = vz;
+    K.cdown[s][d] = cd;
+    K.id[s][d] = id;
   }
 };
 
@@ -620,13 +618,13 @@ __global__ void k_deposit32(DevCtx K, int s, int buf, long long n) {
 size_t push32_smem_bytes(int nx) { return pipes_offset(nx) + sizeof(WarpPipe) * kWarps32; }
 
 cudaError_t launch_push_fp32(const DevCtx& K, int grid, cudaStream_t s) {
-  k_push_fp32<<<grid, kBlock, push32_smem_bytes(K.nx), s>>>(K);
-  return cudaGetLastError();
+  return launch_chained(k_push_fp32, (unsigned)grid, (unsigned)kBlock, push32_smem_bytes(K.nx),
+                        s, K);
 }
 
 cudaError_t launch_place_fp32(const DevCtx& K, int grid, cudaStream_t s) {
-  k_place_field<Fp32Moves><<<grid, 256, sizeof(__int128) * (size_t)K.nx, s>>>(K);
-  return cudaGetLastError();
+  return launch_chained(k_place_field<Fp32Moves>, (unsigned)grid, 256u,
+                        place_smem_bytes(K.nx, K.nlist), s, K);
 }
 
 cudaError_t launch_convert(const DevCtx& K, int species, long long n, bool to_fp32,
@@ -649,10 +647,13 @@ cudaError_t launch_deposit32(const DevCtx& K, int species, int buf, long long n,
 cudaError_t configure_kernels32(int nx) {
   cudaError_t e = cudaFuncSetAttribute(k_push_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)push32_smem_bytes(nx));
-  if (e != cudaSuccess) return e;
+  return e;
+}
+
+cudaError_t configure_place_fp32(int nx, int nlist) {
   return cudaFuncSetAttribute(k_place_field<Fp32Moves>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(__int128) * (size_t)nx));
+                              (int)place_smem_bytes(nx, nlist));
 }
 
 int push_fp32_blocks_per_sm(int nx) {

@@ -406,14 +406,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_push_fp64(DevCtx K) {
   unsigned long long* sCnt = sC + 2 * nx;
   __shared__ int sWarp[kBlock / 32 + 1];
   __shared__ int sRun[3];
-  __shared__ bool sLast;
-  for (int j = threadIdx.x; j < nx; j += blockDim.x) sE[j] = K.E[j];
+  chain_release();  // the placement launch may take the SM room this pass leaves
   for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0ull;
   if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) sRun[0] = sRun[1] = sRun[2] = 0;
+  chain_wait();  // the field and counts of the previous launch are complete
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) sE[j] = K.E[j];
   const unsigned step = K.st->step;
   const long long ne = K.st->n[0], ni = K.st->n[1];
-  if (blockIdx.x == 0 && threadIdx.x == 0) K.st->step_next = step + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) snapshot_pass(K, step, ne, ni);
   __syncthreads();
   const int G = gridDim.x, b = blockIdx.x;
   range_pass<0>(K, step, range_begin(ne, b, G), range_begin(ne, b + 1, G), sE, sC, sC + nx,
@@ -439,35 +440,31 @@ __global__ void __launch_bounds__(kBlock, 2) k_push_fp64(DevCtx K) {
   }
   if (threadIdx.x < kNumCounters && sCnt[threadIdx.x])
     atomicAdd(&K.counters[threadIdx.x], sCnt[threadIdx.x]);
-  // the last block to finish totals the lists (no block waits for another)
-  __threadfence();
-  if (threadIdx.x == 0) sLast = (atomicAdd(&K.st->done_blocks, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (sLast) {
-    __threadfence();
-    // the block's count grids are flushed: their shared memory is the scratch
-    finalize_compaction<kBlock / 32>(K, ne, ni, reinterpret_cast<int*>(sC), 4 * nx);
-  }
 }
 
 // Record moves of the FP64 representation for the placement launch.
 struct Fp64Moves {
+  // every field is loaded before the first store, so the loads are in flight together
   static __device__ __forceinline__ void birth(const DevCtx& K, int s, int list, long long slot,
                                                long long d, unsigned id) {
     const double* rec = list == 0 ? K.eb[0] : (list == 1 ? K.eb[1] : K.ib);
     const size_t cap = (size_t)K.nchunk_max * kChunk;
-    K.x[s][d] = rec[slot];
-    K.vx[s][d] = rec[slot + cap];
-    K.vy[s][d] = rec[slot + 2 * cap];
-    K.vz[s][d] = rec[slot + 3 * cap];
+    const double x = rec[slot], vx = rec[slot + cap], vy = rec[slot + 2 * cap],
+                 vz = rec[slot + 3 * cap];
+    K.x[s][d] = x;
+    K.vx[s][d] = vx;
+    K.vy[s][d] = vy;
+    K.vz[s][d] = vz;
     K.id[s][d] = id;
   }
   static __device__ __forceinline__ void move(const DevCtx& K, int s, long long t, long long d) {
-    K.x[s][d] = K.x[s][t];
-    K.vx[s][d] = K.vx[s][t];
-    K.vy[s][d] = K.vy[s][t];
-    K.vz[s][d] = K.vz[s][t];
-    K.id[s][d] = K.id[s][t];
+    const double x = K.x[s][t], vx = K.vx[s][t], vy = K.vy[s][t], vz = K.vz[s][t];
+    const unsigned id = K.id[s][t];
+    K.x[s][d] = x;
+    K.vx[s][d] = vx;
+    K.vy[s][d] = vy;
+    K.vz[s][d] = vz;
+    K.id[s][d] = id;
   }
 };
 
@@ -497,13 +494,12 @@ cudaError_t launch_field(const DevCtx& K, cudaStream_t s) {
 }
 
 cudaError_t launch_push_fp64(const DevCtx& K, int grid, cudaStream_t s) {
-  k_push_fp64<<<grid, kBlock, push_smem_bytes(K.nx), s>>>(K);
-  return cudaGetLastError();
+  return launch_chained(k_push_fp64, (unsigned)grid, kBlock, push_smem_bytes(K.nx), s, K);
 }
 
 cudaError_t launch_place_fp64(const DevCtx& K, int grid, cudaStream_t s) {
-  k_place_field<Fp64Moves><<<grid, 256, field_smem_bytes(K.nx), s>>>(K);
-  return cudaGetLastError();
+  return launch_chained(k_place_field<Fp64Moves>, (unsigned)grid, 256u,
+                        place_smem_bytes(K.nx, K.nlist), s, K);
 }
 
 cudaError_t launch_set_step(const DevCtx& K, unsigned step, cudaStream_t s) {
@@ -524,11 +520,14 @@ cudaError_t configure_kernels(int nx) {
   cudaError_t e = cudaFuncSetAttribute(k_push_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)push_smem_bytes(nx));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_place_field<Fp64Moves>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem_bytes(nx));
-  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)field_smem_bytes(nx));
+}
+
+cudaError_t configure_place_fp64(int nx, int nlist) {
+  return cudaFuncSetAttribute(k_place_field<Fp64Moves>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)place_smem_bytes(nx, nlist));
 }
 
 int push_fp64_blocks_per_sm(int nx) {

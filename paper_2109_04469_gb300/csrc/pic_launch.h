@@ -24,6 +24,8 @@ cudaError_t launch_max_abs(const double* v, long long n, unsigned long long* out
 int push_fp64_blocks_per_sm(int nx);
 // raise the dynamic shared-memory limit of the grid-sized kernels for nx nodes
 cudaError_t configure_kernels(int nx);
+// the placement launch's shared memory for nx nodes and nlist list owners
+cudaError_t configure_place_fp64(int nx, int nlist);
 
 // FP32 particle path (pic_fp32.cu)
 cudaError_t launch_push_fp32(const DevCtx& K, int grid, cudaStream_t s);
@@ -33,6 +35,7 @@ cudaError_t launch_convert(const DevCtx& K, int species, long long n, bool to_fp
                            cudaStream_t s);
 cudaError_t launch_deposit32(const DevCtx& K, int species, int buf, long long n, cudaStream_t s);
 cudaError_t configure_kernels32(int nx);
+cudaError_t configure_place_fp32(int nx, int nlist);
 int push_fp32_blocks_per_sm(int nx);
 
 }  // namespace pic
