@@ -208,10 +208,8 @@ void carve(const pic_params& p, char* base, DevCtx& K, size_t* total) {
   if (fp32) {
     for (int s = 0; s < 2; ++s) {
       // 64 elements of tail padding: a bulk copy of a last tile is rounded up to 16 bytes
-      K.cell[s] = c.take<unsigned short>(cap + 64);
-      K.cdown[s] = c.take<unsigned short>(cap + 64);
-      K.off[s] = c.take<float>(cap + 64);
-      K.fvx[s] = c.take<float>(cap + 64);
+      K.ccd[s] = c.take<unsigned>(cap + 64);
+      K.ov[s] = c.take<float2>(cap + 64);
       K.fvy[s] = c.take<float>(cap);
       K.fvz[s] = c.take<float>(cap);
       K.feb[s] = c.take<float>(6 * cap);

@@ -112,9 +112,12 @@ struct DevCtx {
   double *ib;           // [4][cap] ion births (FP64 state)
   // FP32 particle state (precision PIC_FP32): position = cell + off in cells, off in [0, 1]
   // (1 only for a particle born on x = L), velocities in cells per step
-  unsigned short* cell[2];
-  unsigned short* cdown[2];  // steps to the next null-collision candidate (bit 15: none)
-  float *off[2], *fvx[2], *fvy[2], *fvz[2];
+  // ccd: cell | countdown << 16, the countdown counting the steps to the next null-collision
+  // candidate (bit 15: the count ran out without a candidate); ov: (off, vx).  The two
+  // arrays the particle pass reads and writes for every particle; vy, vz only on rare paths.
+  unsigned* ccd[2];
+  float2* ov[2];
+  float *fvy[2], *fvz[2];
   float *feb[2], *fib;  // [6][cap] birth records: cell (int bits), off, vx, vy, vz, countdown
   float f_lnq[2];       // ln(1 - P_max) per species (0 without gas)
   const float* fF[2];   // FP32 cumulative collision fractions [kXsNodes][4]

@@ -156,6 +156,7 @@ __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned
                                           unsigned pid, int cell, float off, float vx, bool left,
                                           unsigned* sCe, unsigned long long* sCnt, Rec32* em) {
   const int nc = G->nc;
+  const float vy = G->fvy[S][p], vz = G->fvz[S][p];  // in flight during the draw below
   // the per-step block of the FP64 contract: its third word decides the surface event
   const U4 w = philox4x32_10(pid, step, ((unsigned)S << 30) | ((unsigned)kPurStep << 24), 0u,
                              G->key0, G->key1);
@@ -174,13 +175,11 @@ __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned
       if (!(cell < 0 || (cell == 0 && off == 0.0f) || cell >= nc)) return SurfOut{cell, off, vx, 0};
     }
     atomicAdd(&sCnt[left ? kCnEAbsL : kCnEAbsR], 1ull);
-    const float vy = G->fvy[S][p], vz = G->fvz[S][p];
     const float t = (vx * vx + vy * vy + vz * vz) * G->f_emfac_e * G->f_fedf_inv_de;
     if (t < (float)G->fedf_bins) atomicAdd(&G->fedf[(int)t], 1ull);
     return SurfOut{cell, off, vx, 1};
   }
   atomicAdd(&sCnt[left ? kCnIAbsL : kCnIAbsR], 1ull);
-  const float vy = G->fvy[S][p], vz = G->fvz[S][p];
   const float t = (vx * vx + vy * vy + vz * vz) * G->f_emfac_ilab * G->f_fedf_inv_de;
   if (t < (float)G->fedf_bins) atomicAdd(&G->fedf[G->fedf_bins + (int)t], 1ull);
   int flags = 1;
@@ -218,13 +217,13 @@ __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned
                                           unsigned pid, int cell, float off, float vx,
                                           unsigned cd, unsigned* sCe, unsigned* sCi,
                                           unsigned long long* sCnt, Rec32* re, Rec32* ri) {
+  float vy = G->fvy[S][p], vz = G->fvz[S][p];  // in flight during the draws below
   Stream sc(*G, S, kPurColl, pid, step);
   const U4 wp = philox4x32_10(sc.id, sc.step, sc.base | sc.block, 0u, sc.k0, sc.k1);
   ++sc.block;
   const bool candidate = !(cd & kCdFlag);
   const unsigned cd_next = draw_countdown(u24(wp.b), G->f_lnq[S]);
   if (!candidate) return CollOut{vx, cd_next, 0};
-  float vy = G->fvy[S][p], vz = G->fvz[S][p];
   bool dirty = false;
   int born = 0;
   const float up = u24(wp.a);
@@ -328,36 +327,94 @@ __device__ __forceinline__ void put_rec(float* list, size_t cap, long long slot,
 // A warp's staging of one 128-particle tile (bulk-copy destination; 16-byte aligned fields).
 constexpr int kStages = 3;
 struct WarpTile {
-  unsigned short cell[128], cd[128];
-  float off[128], vx[128];
+  unsigned ccd[128];  // cell | countdown << 16
+  float2 ov[128];     // off, vx
   unsigned id[128];
 };
+// A particle whose countdown ran out (kind 1), or an electron of the EEPF window (kind 2),
+// queued until 32 of them (or the end of the warp's range) are handled together, one per
+// lane, so their scattered loads overlap.
+struct Cand {
+  int p;         // index
+  unsigned ccd;  // cell | countdown << 16
+  float off, vx;
+  unsigned id;
+  int kind;
+};
+constexpr int kCandQ = 64;  // up to 31 waiting + 32 from one row of 32 particles
 struct __align__(128) WarpPipe {  // one per warp, back to back in shared memory
   WarpTile t[kStages];
   unsigned long long bar[kStages];
   Rec32 recE[32], recI[32];  // each lane's births of the current particle
+  Cand cq[kCandQ];
 };
-struct PipeCount {           // per-warp, warp-uniform, in registers
-  long long issued, waited;  // tiles issued / consumed by this warp so far
+struct PipeCount {         // per-warp, warp-uniform, in registers
+  unsigned issued, waited;  // tiles issued / consumed by this warp so far
 };
 
 __device__ __forceinline__ unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
 
-// Lane 0 starts the bulk copies of particles [t0, t0 + n) into the next stage.
+__device__ __forceinline__ bool in_eepf_cells(const DevCtx* __restrict__ G, int cell) {
+  return (unsigned)(cell - G->eepf_jlo) <= (unsigned)(G->eepf_jhi - G->eepf_jlo);
+}
+
+// Handle the first n queued entries (n <= 32, of nq queued), one per lane, in queue order
+// (particle order): for an expiry the collision and next countdown, then the EEPF sample of
+// the (collided) velocity, and the ionization pairs ranked by ballot into the warp's birth
+// lists.  The remaining nq - n entries move to the front of the queue.  Returns the pairs
+// born (the caller advances both birth-list offsets by it).
+template <int S>
+__device__ __noinline__ int drain32(const DevCtx* __restrict__ G, unsigned step, WarpPipe& P,
+                                    int n, int nq, unsigned* sCe, unsigned* sCi,
+                                    unsigned long long* sCnt, long long ek, long long ik) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  bool born = false;
+  if (lane < n) {
+    const Cand c = P.cq[lane];
+    const int cell = (int)(c.ccd & 0xFFFFu);
+    float vx = c.vx;
+    if (c.kind == 1) {
+      const CollOut o = collide32<S>(G, step, c.p, c.id, cell, c.off, c.vx, c.ccd >> 16, sCe,
+                                     sCi, sCnt, &P.recE[lane], &P.recI[lane]);
+      G->ov[S][c.p] = make_float2(c.off, o.vx);
+      G->ccd[S][c.p] = (unsigned)cell | (o.cd << 16);
+      born = o.born != 0;
+      vx = o.vx;
+    }
+    if (S == 0 && in_eepf_cells(G, cell)) eepf32(G, c.p, cell, c.off, vx, sCnt);
+  }
+  int nb = 0;
+  if (S == 0) {
+    const unsigned mb = __ballot_sync(0xffffffffu, born);
+    if (born) {
+      const size_t cap = (size_t)G->nchunk_max * kChunk;
+      put_rec(G->feb[0], cap, ek + __popc(mb & lt), P.recE[lane]);
+      put_rec(G->fib, cap, ik + __popc(mb & lt), P.recI[lane]);
+    }
+    nb = __popc(mb);
+  }
+  __syncwarp();
+  if (lane < nq - n) P.cq[lane] = P.cq[lane + n];  // n == 32 here: disjoint halves
+  __syncwarp();
+  return nb;
+}
+
+// Lane 0 starts the bulk copies of particles [t0, t0 + n) into the next stage (t0 is a
+// multiple of 32, so every source starts on a 16-byte boundary).
 template <int S>
 __device__ __forceinline__ void issue_tile(const DevCtx& K, WarpPipe& P, PipeCount& Q,
                                            long long t0, int n) {
   if ((threadIdx.x & 31) == 0) {
-    const int st = (int)(Q.issued % kStages);
+    const unsigned st = Q.issued % kStages;
     WarpTile& T = P.t[st];
-    const unsigned bh = round16(2u * n), bf = round16(4u * n);
+    const unsigned b4 = round16(4u * n), b8 = round16(8u * n);
     fence_proxy_async_smem();  // the lanes' earlier reads of this stage come first
-    mbar_arrive_expect_tx(&P.bar[st], 2u * bh + 3u * bf);
-    bulk_g2s(T.cell, K.cell[S] + t0, bh, &P.bar[st]);
-    bulk_g2s(T.cd, K.cdown[S] + t0, bh, &P.bar[st]);
-    bulk_g2s(T.off, K.off[S] + t0, bf, &P.bar[st]);
-    bulk_g2s(T.vx, K.fvx[S] + t0, bf, &P.bar[st]);
-    bulk_g2s(T.id, K.id[S] + t0, bf, &P.bar[st]);
+    mbar_arrive_expect_tx(&P.bar[st], 2u * b4 + b8);
+    bulk_g2s(T.ccd, K.ccd[S] + t0, b4, &P.bar[st]);
+    bulk_g2s(T.ov, K.ov[S] + t0, b8, &P.bar[st]);
+    bulk_g2s(T.id, K.id[S] + t0, b4, &P.bar[st]);
   }
   ++Q.issued;
 }
@@ -376,85 +433,143 @@ __device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long
   const int nc = K.nc;
   const size_t cap = (size_t)K.nchunk_max * kChunk;
   const DevCtx* __restrict__ G = K.self;
-  const long long ntiles = (qe - q + 127) / 128;
-  for (long long t = 0; t < kStages - 1 && t < ntiles; ++t)
-    issue_tile<S>(K, P, Q, q + 128 * t, (int)min(128ll, qe - q - 128 * t));
-  for (long long t = 0; t < ntiles; ++t) {
+  const int ntiles = (int)((qe - q + 127) / 128);
+  int nq = 0;          // queued entries (warp-uniform)
+  float fin = 0.0f;    // stays finite unless a velocity was not: v * 0 + fin
+  for (int t = 0; t < kStages - 1 && t < ntiles; ++t)
+    issue_tile<S>(K, P, Q, q + 128 * t, (int)min(128ll, qe - q - 128ll * t));
+  for (int t = 0; t < ntiles; ++t) {
     if (t + kStages - 1 < ntiles) {
-      const long long u = t + kStages - 1;
-      issue_tile<S>(K, P, Q, q + 128 * u, (int)min(128ll, qe - q - 128 * u));
+      const int u = t + kStages - 1;
+      issue_tile<S>(K, P, Q, q + 128ll * u, (int)min(128ll, qe - q - 128ll * u));
     }
-    const int st = (int)(Q.waited % kStages);
-    if (!mbar_wait(&P.bar[st], (unsigned)((Q.waited / kStages) & 1))) {
+    const unsigned st = Q.waited % kStages;
+    if (!mbar_wait(&P.bar[st], (Q.waited / kStages) & 1u)) {
       atomicOr(&K.st->status, kStTimeout);
-      for (long long w = Q.waited + 1; w < Q.issued; ++w)  // let the copies in flight land
-        (void)mbar_wait(&P.bar[w % kStages], (unsigned)((w / kStages) & 1));
+      for (unsigned w = Q.waited + 1; w < Q.issued; ++w)  // let the copies in flight land
+        (void)mbar_wait(&P.bar[w % kStages], (w / kStages) & 1u);
       Q.waited = Q.issued;
       return false;
     }
     ++Q.waited;
     const WarpTile& T = P.t[st];
-    const long long tile = q + 128 * t;
-#pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-      const int ix = 32 * k + lane;
-      const long long p = tile + ix;
-      bool dead = false, be = false, bi = false;
-      if (p < qe) {
-        int cell = T.cell[ix];
-        float off = T.off[ix];
-        float vx = T.vx[ix];
-        unsigned cd = T.cd[ix];
-        // steps 3-4: gather (linear) and leapfrog in cell units
-        const float2 e = sE[cell];
-        vx += e.x + off * e.y;
-        off += vx;
-        renorm(cell, off);
-        if (!isfinite(vx)) atomicOr(&K.st->status, kStNonfinite);
-        const bool out_l = cell < 0 || (cell == 0 && off == 0.0f);
-        if (out_l || cell >= nc) {
-          const SurfOut r = surface32<S>(G, step, p, T.id[ix], cell, off, vx, out_l, sCe, sCnt,
-                                         &P.recE[lane]);
-          cell = r.cell;
-          off = r.off;
-          vx = r.vx;
-          dead = r.flags & 1;
-          be = (r.flags >> 1) & 1;
-        }
-        if (!dead) {
-          // step 6: the countdown to the next null-collision candidate
-          --cd;
-          if ((cd & 0x7FFFu) == 0u) {
-            const CollOut c = collide32<S>(G, step, p, T.id[ix], cell, off, vx, cd, sCe, sCi,
-                                           sCnt, &P.recE[lane], &P.recI[lane]);
-            vx = c.vx;
-            cd = c.cd;
-            bi = c.born != 0;
-            if (S == 0) be = bi;  // an ionization pair
-          }
-          deposit32(S == 0 ? sCe : sCi, cell, off);
-          if (S == 0 && cell >= K.eepf_jlo && cell <= K.eepf_jhi) eepf32(G, p, cell, off, vx, sCnt);
-        }
-        K.cell[S][p] = (unsigned short)cell;
-        K.off[S][p] = off;
-        K.fvx[S][p] = vx;
-        K.cdown[S][p] = (unsigned short)cd;
+    const long long tile = q + 128ll * t;
+    const int nv = (int)min(128ll, qe - tile);  // particles of this tile
+    unsigned* __restrict__ gccd = K.ccd[S] + tile;
+    float2* __restrict__ gov = K.ov[S] + tile;
+    // Each lane owns particles 32 j + lane (j = 0..3), so the tile is walked in particle
+    // order j-major, lane-minor; the common path of the four runs interleaved.
+    // steps 3-4: linear gather and leapfrog in cell units
+    int cell[4];
+    float off[4], vx[4];
+    unsigned cd[4];
+    unsigned outm = 0u;  // bit j: particle j left the gap
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ix = 32 * j + lane;
+      const bool valid = ix < nv;
+      const unsigned cc = T.ccd[ix];
+      const float2 ov = T.ov[ix];
+      cell[j] = valid ? (int)(cc & 0xFFFFu) : 0;  // staged entries past nv are not this range's
+      cd[j] = cc >> 16;
+      off[j] = ov.x;
+      vx[j] = ov.y;
+      const float2 e = sE[cell[j]];
+      vx[j] += e.x + off[j] * e.y;
+      off[j] += vx[j];
+      renorm(cell[j], off[j]);
+      if (valid) {
+        fin = fmaf(vx[j], 0.0f, fin);
+        if ((unsigned)cell[j] >= (unsigned)nc || (cell[j] == 0 && off[j] == 0.0f)) outm |= 1u << j;
       }
-      // particle order within the warp tile is (k, lane): rank by ballot
-      if (__any_sync(0xffffffffu, dead || be || (S == 0 && bi))) {
-        const unsigned mh = __ballot_sync(0xffffffffu, dead);
-        const unsigned me = __ballot_sync(0xffffffffu, be);
-        const unsigned mi = __ballot_sync(0xffffffffu, S == 0 && bi);
-        if (dead) K.hole_idx[S][hk + __popc(mh & lt)] = (int)p;
-        if (be) put_rec(K.feb[S], cap, ek + __popc(me & lt), P.recE[lane]);
-        if (S == 0 && bi) put_rec(K.fib, cap, ik + __popc(mi & lt), P.recI[lane]);
-        hk += __popc(mh);
-        ek += __popc(me);
-        ik += __popc(mi);
+    }
+    // step 5 (rare): surfaces, holes and ion-induced electrons ranked in particle order
+    unsigned deadm = 0u;
+    if (__any_sync(0xffffffffu, outm != 0u)) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool out = (outm >> j) & 1u;
+        if (__any_sync(0xffffffffu, out)) {
+          const long long p = tile + 32 * j + lane;
+          bool dead = false, be = false;
+          if (out) {
+            const bool out_l = cell[j] < 0 || (cell[j] == 0 && off[j] == 0.0f);
+            const SurfOut r = surface32<S>(G, step, p, T.id[32 * j + lane], cell[j], off[j],
+                                           vx[j], out_l, sCe, sCnt, &P.recE[lane]);
+            cell[j] = r.cell;
+            off[j] = r.off;
+            vx[j] = r.vx;
+            dead = r.flags & 1;
+            be = (r.flags >> 1) & 1;
+          }
+          const unsigned mh = __ballot_sync(0xffffffffu, dead);
+          const unsigned me = __ballot_sync(0xffffffffu, be);
+          if (dead) K.hole_idx[S][hk + __popc(mh & lt)] = (int)p;
+          if (be) put_rec(K.feb[S], cap, ek + __popc(me & lt), P.recE[lane]);
+          hk += __popc(mh);
+          ek += __popc(me);
+          deadm |= (unsigned)dead << j;
+        }
+      }
+    }
+    // step 6: the countdown to the next null-collision candidate, then the deposit (the
+    // collision changes neither cell nor offset).  An expiry is queued (kind 1), as is an
+    // electron in the EEPF cells (kind 2); their velocity and countdown are rewritten by the
+    // drain, after the stores below.
+    unsigned expm = 0u, eepm = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ix = 32 * j + lane;
+      if (ix < nv && !((deadm >> j) & 1u)) {
+        --cd[j];
+        const bool ex = (cd[j] & 0x7FFFu) == 0u;
+        expm |= (unsigned)ex << j;
+        deposit32(S == 0 ? sCe : sCi, cell[j], off[j]);
+        if (S == 0 && !ex && in_eepf_cells(G, cell[j])) eepm |= 1u << j;
+      }
+    }
+    if (nv == 128) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        gccd[32 * j + lane] = ((unsigned)cell[j] & 0xFFFFu) | (cd[j] << 16);
+        gov[32 * j + lane] = make_float2(off[j], vx[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (32 * j + lane < nv) {
+          gccd[32 * j + lane] = ((unsigned)cell[j] & 0xFFFFu) | (cd[j] << 16);
+          gov[32 * j + lane] = make_float2(off[j], vx[j]);
+        }
+    }
+    if (__any_sync(0xffffffffu, (expm | eepm) != 0u)) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool qj = ((expm | eepm) >> j) & 1u;
+        const unsigned mq = __ballot_sync(0xffffffffu, qj);
+        if (mq) {
+          if (qj)
+            P.cq[nq + __popc(mq & lt)] =
+                Cand{(int)(tile + 32 * j + lane), ((unsigned)cell[j] & 0xFFFFu) | (cd[j] << 16),
+                     off[j], vx[j], T.id[32 * j + lane], ((expm >> j) & 1u) ? 1 : 2};
+          nq += __popc(mq);
+          if (nq >= 32) {
+            const int nb = drain32<S>(G, step, P, 32, nq, sCe, sCi, sCnt, ek, ik);
+            ek += nb;
+            ik += nb;
+            nq -= 32;
+          }
+        }
       }
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
   }
+  if (nq > 0) {
+    const int nb = drain32<S>(G, step, P, nq, nq, sCe, sCi, sCnt, ek, ik);
+    ek += nb;
+    ik += nb;
+  }
+  if (__any_sync(0xffffffffu, !isfinite(fin)) && lane == 0) atomicOr(&K.st->status, kStNonfinite);
   return true;
 }
 
@@ -520,7 +635,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
     for (int s = 0; s < kStages; ++s) mbar_init(&P.bar[s], 1u);
     fence_mbar_init();
   }
-  PipeCount Q{0, 0};
+  PipeCount Q{0u, 0u};
   for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0u;
   if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
   chain_wait();  // the kick tables and counts of the previous launch are complete
@@ -552,24 +667,21 @@ struct Fp32Moves {
     const size_t cap = (size_t)K.nchunk_max * kChunk;
     const float c = rec[slot], o = rec[slot + cap], vx = rec[slot + 2 * cap],
                 vy = rec[slot + 3 * cap], vz = rec[slot + 4 * cap], cd = rec[slot + 5 * cap];
-    K.cell[s][d] = (unsigned short)__float_as_int(c);
-    K.off[s][d] = o;
-    K.fvx[s][d] = vx;
+    K.ccd[s][d] = (unsigned)__float_as_int(c) | ((unsigned)__float_as_int(cd) << 16);
+    K.ov[s][d] = make_float2(o, vx);
     K.fvy[s][d] = vy;
     K.fvz[s][d] = vz;
-    K.cdown[s][d] = (unsigned short)__float_as_int(cd);
     K.id[s][d] = id;
   }
   static __device__ __forceinline__ void move(const DevCtx& K, int s, long long t, long long d) {
-    const unsigned short c = K.cell[s][t], cd = K.cdown[s][t];
-    const float o = K.off[s][t], vx = K.fvx[s][t], vy = K.fvy[s][t], vz = K.fvz[s][t];
+    const unsigned ccd = K.ccd[s][t];
+    const float2 ov = K.ov[s][t];
+    const float vy = K.fvy[s][t], vz = K.fvz[s][t];
     const unsigned id = K.id[s][t];
-    K.cell[s][d] = c;
-    K.off[s][d] = o;
-    K.fvx[s][d] = vx;
+    K.ccd[s][d] = ccd;
+    K.ov[s][d] = ov;
     K.fvy[s][d] = vy;
     K.fvz[s][d] = vz;
-    K.cdown[s][d] = cd;
     K.id[s][d] = id;
   }
 };
@@ -583,22 +695,21 @@ __global__ void k_to_fp32(DevCtx K, int s, long long n) {
   long long j = __double2ll_rd(xn);
   if (j > K.nc - 1) j = K.nc - 1;
   if (j < 0) j = 0;
-  K.cell[s][q] = (unsigned short)j;
-  K.off[s][q] = (float)(xn - (double)j);
   const double sc = K.dt * K.inv_dx;  // m/s -> cells per step
-  K.fvx[s][q] = (float)(K.vx[s][q] * sc);
+  K.ov[s][q] = make_float2((float)(xn - (double)j), (float)(K.vx[s][q] * sc));
   K.fvy[s][q] = (float)(K.vy[s][q] * sc);
   K.fvz[s][q] = (float)(K.vz[s][q] * sc);
   Stream st(K, s, kPurCount, K.id[s][q], K.st->step);
-  K.cdown[s][q] = draw_countdown(next_u(st), K.f_lnq[s]);
+  K.ccd[s][q] = (unsigned)j | ((unsigned)draw_countdown(next_u(st), K.f_lnq[s]) << 16);
 }
 
 // FP32 cell units -> FP64 SI state, for pic_get_particles and the diagnostics.
 __global__ void k_to_fp64(DevCtx K, int s, long long n) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  K.x[s][q] = ((double)K.cell[s][q] + (double)K.off[s][q]) * K.dx;
-  K.vx[s][q] = (double)K.fvx[s][q] * K.to_si_v;
+  const float2 ov = K.ov[s][q];
+  K.x[s][q] = ((double)(K.ccd[s][q] & 0xFFFFu) + (double)ov.x) * K.dx;
+  K.vx[s][q] = (double)ov.y * K.to_si_v;
   K.vy[s][q] = (double)K.fvy[s][q] * K.to_si_v;
   K.vz[s][q] = (double)K.fvz[s][q] * K.to_si_v;
 }
@@ -607,8 +718,8 @@ __global__ void k_to_fp64(DevCtx K, int s, long long n) {
 __global__ void k_deposit32(DevCtx K, int s, int buf, long long n) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  const int j = K.cell[s][q];
-  const int wr = __float2int_rn(K.off[s][q] * 65536.0f);
+  const int j = (int)(K.ccd[s][q] & 0xFFFFu);
+  const int wr = __float2int_rn(K.ov[s][q].x * 65536.0f);
   unsigned long long* C = K.C + (size_t)(buf * 2 + s) * K.nx;
   atomicAdd(&C[j], (unsigned long long)(65536 - wr) << 16);
   atomicAdd(&C[j + 1], (unsigned long long)wr << 16);

@@ -7,7 +7,11 @@
 
 namespace pic {
 
-constexpr long long kSpinLimit = 1ll << 24;  // polls of a bulk-copy barrier (~seconds)
+// A wait polls the barrier with a suspend-time hint: the warp sleeps until the phase
+// completes or the hint expires, so a poll costs a few instructions per wake-up, not per
+// spin.  kSpinLimit polls bound the wait (about kSpinLimit x kSuspendNs at worst).
+constexpr long long kSpinLimit = 4000;
+constexpr unsigned kSuspendNs = 500000;  // 0.5 ms
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -49,10 +53,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   unsigned ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0u;
 }
