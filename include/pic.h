@@ -138,6 +138,12 @@ int pic_set_particles(pic_handle* h, int species, const double* x, const double*
 /* Number of particles of each species (synchronises). */
 int pic_counts(pic_handle* h, int64_t* n_e, int64_t* n_i);
 
+/* Enqueue on the handle's stream a copy of the two particle counts (electrons, ions) as they
+ * stand when the stream reaches it into counts2[2], without synchronising.  counts2 should be
+ * pinned host memory (cudaHostAlloc), else the copy is synchronous; it must stay valid until
+ * the stream has passed the copy. */
+int pic_counts_async(pic_handle* h, int64_t* counts2);
+
 /* Copy the current charge counts (int64, 2^32 per superparticle, [n_cells+1] each) and the
  * potential / field of the current step (solved from those counts at the end of the
  * previous step, at init, or by pic_solve_field) to host arrays (any may be NULL).

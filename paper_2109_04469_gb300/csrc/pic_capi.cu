@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -513,6 +514,14 @@ int pic_counts(pic_handle* h, int64_t* n_e, int64_t* n_i) {
   PIC_CUDA(cudaMemcpy(&s, h->K.st, sizeof s, cudaMemcpyDeviceToHost));
   if (n_e) *n_e = s.n[0];
   if (n_i) *n_i = s.n[1];
+  return PIC_OK;
+}
+
+int pic_counts_async(pic_handle* h, int64_t* counts2) {
+  if (!h || !counts2) return PIC_ERR_PARAM;
+  static_assert(offsetof(DevState, n) == 0, "counts lead the device state");
+  PIC_CUDA(cudaMemcpyAsync(counts2, h->K.st, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                           h->stream));
   return PIC_OK;
 }
 

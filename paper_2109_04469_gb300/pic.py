@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
                 "pic_get_particles": (C.c_int, [P, C.c_int, P, P, P, P, P, i64, C.POINTER(i64)]),
                 "pic_set_particles": (C.c_int, [P, C.c_int, P, P, P, P, P, i64, u32]),
                 "pic_counts": (C.c_int, [P, C.POINTER(i64), C.POINTER(i64)]),
+                "pic_counts_async": (C.c_int, [P, P]),
                 "pic_get_grid": (C.c_int, [P, P, P, P, P]),
                 "pic_solve_field": (C.c_int, [P]),
                 "pic_get_accum": (C.c_int, [P, P, P, P, P, P, P, C.POINTER(i64)]),
@@ -200,6 +201,14 @@ class Simulation:
         a, b = C.c_int64(), C.c_int64()
         _check(lib().pic_counts(self._h, C.byref(a), C.byref(b)), "pic_counts")
         return a.value, b.value
+
+    def counts_async(self, out) -> None:
+        """Enqueue a copy of the two counts into `out` (a pinned host int64 tensor of 2)."""
+        import torch
+
+        if out.dtype != torch.int64 or out.numel() < 2 or out.is_cuda or not out.is_contiguous():
+            raise ValueError("counts_async: a contiguous host int64 tensor of 2 expected")
+        _check(lib().pic_counts_async(self._h, C.c_void_p(out.data_ptr())), "pic_counts_async")
 
     def step_state(self) -> tuple[int, int, int]:
         s, e, i = C.c_uint32(), C.c_uint32(), C.c_uint32()
