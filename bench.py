@@ -205,9 +205,8 @@ BYTES_PER_PARTICLE = {  # algorithmic bytes of the particle pass per particle-st
     # FP64: x, vx read and written (32 B) + id read (4 B); a candidate also reads and writes
     # vy, vz (32 B); a removed or born particle moves one 36 B record
     "fp64": (36.0, 32.0, 36.0),
-    # FP32: offset, vx read and written (16 B) + 16-bit cell and countdown read and written
-    # (8 B) + id read
-    # (4 B); candidates r/w vy, vz (16 B); a moved record is 24 B
+    # FP32: (offset, vx) read and written (16 B) + cell|countdown u32 read and written (8 B)
+    # + id read (4 B); candidates r/w vy, vz (16 B); a moved record is 24 B
     "fp32": (28.0, 16.0, 24.0),
 }
 
