@@ -299,12 +299,13 @@ def measure(pcfg: dict, precision: str, args, torch, dist, local_rank: int,
     return out
 
 
-def reduce_ranks(torch, dist, step_ms: float, parts: int):
+def reduce_ranks(torch, dist, step_ms: float, parts: int, device: str = "cuda"):
+    """Whole-job figures of the replicas: the slowest rank's time, every rank's particles."""
     if not dist:
         return step_ms, parts
-    t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    p = torch.tensor([float(parts)], dtype=torch.float64, device="cuda")
+    p = torch.tensor([int(parts)], dtype=torch.int64, device=device)
     dist.all_reduce(p, op=dist.ReduceOp.SUM)
     return float(t.item()), int(p.item())
 
