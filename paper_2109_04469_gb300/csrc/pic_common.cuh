@@ -289,41 +289,39 @@ __device__ __forceinline__ int find_sorted(const int* a, int n, long long v, boo
 // prefix arrays of the other blocks.
 __host__ __device__ __forceinline__ size_t place_smem_bytes(int nx, int nlist) {
   const size_t field = sizeof(__int128) * (size_t)nx;
-  const size_t lists = sizeof(int) * (5 * (size_t)nlist + 4);  // + rounding of 16-B loads
+  const size_t lists = sizeof(int) * 5 * (size_t)((nlist + 3) & ~3);  // 16-byte rows
   return field > lists ? field : lists;
 }
 
+// Row stride, in ints, of the five prefix arrays in shared memory (16-byte rows).
+__host__ __device__ __forceinline__ int prefix_stride(int G) { return (G + 3) & ~3; }
+
 // Reading C-15, run by every placement block into its own shared memory: the exclusive
-// prefixes of the five per-owner count arrays (sp[a * G + c]: a = 0, 1 holes of electrons /
-// ions; 2 electron births from electron ranges; 3 electron births from ion ranges, whose
-// ranks continue those of list 2; 4 ion births) and the totals of both species.  The counts
-// of the particle pass are read once with coalesced loads; nothing waits on another block.
+// prefixes of the five per-owner count arrays of one simulation (sp[a * Gp + c], Gp =
+// prefix_stride(G): a = 0, 1 holes of electrons / ions; 2 electron births from electron
+// ranges; 3 electron births from ion ranges, whose ranks continue those of list 2; 4 ion
+// births) and the totals of both species.  The count arrays lie at stride gstride from
+// hole_cnt[0] (gstride >= G + 4 or the block is padded); they are read once with 16-byte
+// loads; nothing waits on another block.
 template <int NT>
-__device__ void list_prefixes(const DevCtx& K, int* sp, CompactTot* sT) {
-  constexpr int kA = 5, NW = NT / 32, kBatch = 12;
+__device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, CompactTot* sT) {
+  constexpr int kA = 5, NW = NT / 32;
   __shared__ int wsum[NW][kA], wtot[kA];
   __shared__ int sq[2];
-  const int G = K.nlist;  // list owners: particle blocks (FP64 pass) or warps (FP32 pass)
+  const int Gp = prefix_stride(G);
   const long long N2[2] = {K.st->n_snap[0], K.st->n_snap[1]};  // loads overlap the staging
   const unsigned nid2[2] = {K.st->id_snap[0], K.st->id_snap[1]};
-  // the five count arrays lie contiguously at stride G from hole_cnt[0] (16-byte aligned,
-  // padded): one pass of 16-byte loads, all in flight together for up to 12 per thread
-  {
-    const int4* src = reinterpret_cast<const int4*>(K.hole_cnt[0]);
-    int4* dst = reinterpret_cast<int4*>(sp);
-    const int n4 = (kA * G + 3) / 4;
-    for (int i0 = threadIdx.x; i0 < n4; i0 += kBatch * NT) {
-      int4 v[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int i = i0 + u * NT;
-        if (i < n4) v[u] = __ldcg(src + i);
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int i = i0 + u * NT;
-        if (i < n4) dst[i] = v[u];
-      }
+  if ((gstride & 3) == 0) {  // rows start on 16-byte boundaries: 16-byte loads, all in flight
+    const int n4 = Gp / 4;
+    for (int i = threadIdx.x; i < kA * n4; i += NT) {
+      const int a = i / n4, c = i - a * n4;
+      reinterpret_cast<int4*>(sp + a * Gp)[c] =
+          __ldcg(reinterpret_cast<const int4*>(K.hole_cnt[0] + (size_t)a * gstride) + c);
+    }
+  } else {
+    for (int i = threadIdx.x; i < kA * G; i += NT) {
+      const int a = i / G, c = i - a * G;
+      sp[a * Gp + c] = __ldcg(K.hole_cnt[0] + (size_t)a * gstride + c);
     }
   }
   if (threadIdx.x < 2) sq[threadIdx.x] = 0;
@@ -335,7 +333,7 @@ __device__ void list_prefixes(const DevCtx& K, int* sp, CompactTot* sT) {
 #pragma unroll
   for (int a = 0; a < kA; ++a) {
     loc[a] = 0;
-    for (int c = c0; c < c1; ++c) loc[a] += sp[a * G + c];
+    for (int c = c0; c < c1; ++c) loc[a] += sp[a * Gp + c];
     inc[a] = loc[a];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -359,8 +357,8 @@ __device__ void list_prefixes(const DevCtx& K, int* sp, CompactTot* sT) {
   for (int a = 0; a < kA; ++a) {
     int run = wsum[w][a] + inc[a] - loc[a] + (a == 3 ? wtot[2] : 0);
     for (int c = c0; c < c1; ++c) {
-      const int v = sp[a * G + c];
-      sp[a * G + c] = run;
+      const int v = sp[a * Gp + c];
+      sp[a * Gp + c] = run;
       run += v;
     }
   }
@@ -380,7 +378,7 @@ __device__ void list_prefixes(const DevCtx& K, int* sp, CompactTot* sT) {
       const int b = range_owner(N2[s], Nn2[s], G);
       owner[s] = b;
       const int* list = K.hole_idx[s] + list_base(N2[s], b, G);
-      const int m = (b + 1 < G ? sp[s * G + b + 1] : H2[s]) - sp[s * G + b];
+      const int m = (b + 1 < G ? sp[s * Gp + b + 1] : H2[s]) - sp[s * Gp + b];
       unsigned below = 0;
       for (int r = threadIdx.x; r < m; r += NT) below += ((long long)list[r] < Nn2[s]) ? 1u : 0u;
       below = __reduce_add_sync(0xffffffffu, below);
@@ -397,7 +395,7 @@ __device__ void list_prefixes(const DevCtx& K, int* sp, CompactTot* sT) {
     t.B0 = s ? wtot[4] : wtot[2];
     t.Beff = Beff2[s];
     t.Nn = Nn2[s];
-    t.q = owner[s] >= 0 ? (long long)sp[s * G + owner[s]] + sq[s] : 0;
+    t.q = owner[s] >= 0 ? (long long)sp[s * Gp + owner[s]] + sq[s] : 0;
     t.nid = nid2[s];
     t.pad = 0;
     sT[s] = t;
@@ -405,46 +403,44 @@ __device__ void list_prefixes(const DevCtx& K, int* sp, CompactTot* sT) {
   __syncthreads();
 }
 
-// Index of the hole of rank r of species s (hp: that species' hole prefixes).
-__device__ __forceinline__ long long hole_of_rank(const DevCtx& K, const int* hp, int s,
+// Index of the hole of rank r of species s (hp: that species' hole prefixes, G owners).
+__device__ __forceinline__ long long hole_of_rank(const DevCtx& K, int G, const int* hp, int s,
                                                   long long r, const CompactTot& t) {
-  const int b = upper_bound_i(hp, K.nlist, r) - 1;
-  return K.hole_idx[s][list_base(t.N, b, K.nlist) + (r - hp[b])];
+  const int b = upper_bound_i(hp, G, r) - 1;
+  return K.hole_idx[s][list_base(t.N, b, G) + (r - hp[b])];
 }
 
-// Placement launch: block 0 advances the field; the other blocks each total the lists, then
-// place every birth (into the holes by rank, then after N) and move every tail survivor
-// (index >= Nn, not a hole) into the remaining holes below Nn, in ascending order.  Block 1
-// publishes the new counts and id counters.  P supplies the record moves of the particle
-// representation: P::birth(K, s, list, slot, d, id) and P::move(K, s, t, d).
-template <class P>
-__global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
-  extern __shared__ __align__(16) unsigned char place_smem[];
-  chain_release();  // the next particle pass may take the SM room this launch leaves
-  chain_wait();     // the particle pass of this step has completed
-  if (blockIdx.x == 0) {
-    advance_field(K, place_smem);
-    return;
-  }
-  __shared__ CompactTot sT[2];
-  int* sp = reinterpret_cast<int*>(place_smem);
-  list_prefixes<256>(K, sp, sT);
-  const CompactTot &te = sT[0], &ti = sT[1];  // shared: no per-thread copies
-  if (blockIdx.x == 1 && threadIdx.x < 2) {
-    const CompactTot& t = sT[threadIdx.x];
-    K.st->n[threadIdx.x] = t.Nn;
-    K.st->next_id[threadIdx.x] = t.nid + (unsigned)t.Beff;
-    if (t.B > t.Beff) {
-      atomicOr(&K.st->status, kStCapacity);
-      atomicAdd(&K.counters[kCnDropped], (unsigned long long)(t.B - t.Beff));
-    }
-  }
-  const int G = K.nlist;
+// Births and tail survivors of one simulation to place: births into the holes by rank, then
+// after N; tail survivors (index >= Nn, not a hole) into the remaining holes below Nn.
+__device__ __forceinline__ long long place_count(const CompactTot* sT) {
+  const CompactTot &te = sT[0], &ti = sT[1];
   const long long tle = te.H > te.Beff ? te.N - te.Nn : 0;
   const long long tli = ti.H > ti.Beff ? ti.N - ti.Nn : 0;
-  const long long n_items = te.Beff + tle + ti.Beff + tli;
-  for (long long u = (long long)(blockIdx.x - 1) * blockDim.x + threadIdx.x; u < n_items;
-       u += (long long)(gridDim.x - 1) * blockDim.x) {
+  return te.Beff + tle + ti.Beff + tli;
+}
+
+// The new counts and id counters of a simulation (and the births dropped at capacity).
+__device__ __forceinline__ void publish_counts(const DevCtx& K, int s, const CompactTot& t) {
+  K.st->n[s] = t.Nn;
+  K.st->next_id[s] = t.nid + (unsigned)t.Beff;
+  if (t.B > t.Beff) {
+    atomicOr(&K.st->status, kStCapacity);
+    atomicAdd(&K.counters[kCnDropped], (unsigned long long)(t.B - t.Beff));
+  }
+}
+
+// Items u = first, first + step, ... below end of the placement of one simulation (items in
+// the order: electron births, electron tail moves, ion births, ion tail moves).  P supplies
+// the record moves of the particle representation: P::birth(K, s, list, slot, d, id) and
+// P::move(K, s, t, d).
+template <class P>
+__device__ __forceinline__ void place_items(const DevCtx& K, int G, const int* sp,
+                                            const CompactTot* sT, long long first,
+                                            long long end, long long step) {
+  const int Gp = prefix_stride(G);
+  const CompactTot &te = sT[0], &ti = sT[1];  // shared: no per-thread copies
+  const long long tle = te.H > te.Beff ? te.N - te.Nn : 0;
+  for (long long u = first; u < end; u += step) {
     long long v = u;
     int s;
     bool birth;
@@ -459,7 +455,7 @@ __global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
       s = 1; birth = false;
     }
     const CompactTot& t = sT[s];
-    const int* hp = sp + s * G;
+    const int* hp = sp + s * Gp;
     if (birth) {
       const long long r = v;
       int list, b;
@@ -468,18 +464,18 @@ __global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
       // (emission); ion births from the electron ranges
       if (s == 0 && r < t.B0) {
         list = 0;
-        b = upper_bound_i(sp + 2 * G, G, r) - 1;
-        slot = list_base(te.N, b, G) + (r - sp[2 * G + b]);
+        b = upper_bound_i(sp + 2 * Gp, G, r) - 1;
+        slot = list_base(te.N, b, G) + (r - sp[2 * Gp + b]);
       } else if (s == 0) {
         list = 1;
-        b = upper_bound_i(sp + 3 * G, G, r) - 1;
-        slot = list_base(ti.N, b, G) + (r - sp[3 * G + b]);
+        b = upper_bound_i(sp + 3 * Gp, G, r) - 1;
+        slot = list_base(ti.N, b, G) + (r - sp[3 * Gp + b]);
       } else {
         list = 2;
-        b = upper_bound_i(sp + 4 * G, G, r) - 1;
-        slot = list_base(te.N, b, G) + (r - sp[4 * G + b]);
+        b = upper_bound_i(sp + 4 * Gp, G, r) - 1;
+        slot = list_base(te.N, b, G) + (r - sp[4 * Gp + b]);
       }
-      const long long d = (r < t.H) ? hole_of_rank(K, hp, s, r, t) : t.N + r - t.H;
+      const long long d = (r < t.H) ? hole_of_rank(K, G, hp, s, r, t) : t.N + r - t.H;
       P::birth(K, s, list, slot, d, t.nid + (unsigned)r);
     } else {
       const long long idx = t.Nn + v;  // a tail position
@@ -491,9 +487,28 @@ __global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
       if (is_hole) continue;  // the tail position is itself a hole
       const long long before = (long long)hp[b] + lb;  // holes below idx
       const long long j = (idx - t.Nn) - (before - t.q);  // rank among survivors
-      P::move(K, s, idx, hole_of_rank(K, hp, s, t.Beff + j, t));
+      P::move(K, s, idx, hole_of_rank(K, G, hp, s, t.Beff + j, t));
     }
   }
+}
+
+// Placement launch: block 0 advances the field; the other blocks each total the lists and
+// place the births and tail survivors; block 1 publishes the new counts and id counters.
+template <class P>
+__global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
+  extern __shared__ __align__(16) unsigned char place_smem[];
+  chain_release();  // the next particle pass may take the SM room this launch leaves
+  chain_wait();     // the particle pass of this step has completed
+  if (blockIdx.x == 0) {
+    advance_field(K, place_smem);
+    return;
+  }
+  __shared__ CompactTot sT[2];
+  int* sp = reinterpret_cast<int*>(place_smem);
+  list_prefixes<256>(K, K.nlist, K.nlist, sp, sT);
+  if (blockIdx.x == 1 && threadIdx.x < 2) publish_counts(K, threadIdx.x, sT[threadIdx.x]);
+  place_items<P>(K, K.nlist, sp, sT, (long long)(blockIdx.x - 1) * blockDim.x + threadIdx.x,
+                 place_count(sT), (long long)(gridDim.x - 1) * blockDim.x);
 }
 
 }  // namespace pic
