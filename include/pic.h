@@ -183,6 +183,60 @@ void pic_free(pic_handle* h);
 /* Static string for a return code. */
 const char* pic_strerror(int code);
 
+/* Description of the last CUDA error that a call made on this thread turned into
+ * PIC_ERR_CUDA ("no CUDA error" if none). */
+const char* pic_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Ensembles: the paper's parameter scans (§3 varies N_t, N_x, W, R and γ around its base
+ * cases) as many independent FP32 simulations advanced together, one cooperative launch per
+ * step (replayed from a CUDA graph).  Each member is an ordinary PIC_FP32 handle made by
+ * pic_init (its own parameters and workspace); all members must share one CUDA stream.
+ * Every single-run call (pic_diag, pic_get_particles, ...) still works on a member.  A member
+ * is advanced by pic_ensemble_step until its step index reaches its target, then left alone.
+ * The results do not depend on the ensemble's schedule (owner size, grid, graph): the
+ * compaction rule fixes every slot, and deposits are integer sums, so a member advanced in an
+ * ensemble is bit for bit the same simulation advanced alone with pic_step.
+ * --------------------------------------------------------------------------------------- */
+typedef struct pic_ensemble pic_ensemble;
+#define PIC_MAX_ENSEMBLE 128
+
+/* Device workspace of an ensemble of n members (1 <= n <= PIC_MAX_ENSEMBLE). */
+int pic_ensemble_workspace_bytes(int n, size_t* bytes);
+
+/* Make an ensemble of the n handles sims[] (PIC_FP32, one stream, distinct) in the caller's
+ * DEVICE workspace (256-byte aligned, kept alive until pic_ensemble_free; the members'
+ * workspaces likewise).  target_steps[i] >= 0: the step index at which member i stops.
+ * Records the step launch as a CUDA graph (falls back to direct launches if recording
+ * fails).  Synchronises the stream.  PIC_ERR_PARAM for a member that is not PIC_FP32, on
+ * another stream or repeated; PIC_ERR_WORKSPACE for a missing or small workspace. */
+int pic_ensemble_create(pic_handle* const* sims, int n, const int64_t* target_steps,
+                        void* workspace, size_t workspace_bytes, pic_ensemble** out);
+
+/* Enqueue n_steps ensemble steps (each advances every member below its target by one step,
+ * §2 steps 1-6) without synchronising; returns the status seen by an earlier sync. */
+int pic_ensemble_step(pic_ensemble* e, int64_t n_steps);
+
+/* Wait for the stream; the ensemble's status (PIC_ERR_TIMEOUT if its grid barrier ran out),
+ * else the first non-OK member status. */
+int pic_ensemble_sync(pic_ensemble* e);
+
+/* Schedule: particles per list owner (256..4000), blocks per SM (1 or 2, as resources allow)
+ * and whether to replay a CUDA graph.  Synchronises.  Results do not depend on it. */
+int pic_ensemble_configure(pic_ensemble* e, int32_t unit, int32_t blocks_per_sm,
+                           int32_t use_graph);
+
+/* Time each schedule of the tuning space (unit 1024 / 2048 / 4000 x 1..2 blocks per SM)
+ * over trial_steps real steps of the ensemble (the members advance by those steps) and keep
+ * the fastest; chosen[0] = unit, chosen[1] = blocks per SM (chosen may be NULL). */
+int pic_ensemble_autotune(pic_ensemble* e, int32_t trial_steps, int32_t* chosen);
+
+/* out[5]: unit, blocks per SM, grid size, graph replay (0/1), dynamic shared memory bytes. */
+int pic_ensemble_info(pic_ensemble* e, int32_t* out);
+
+/* Release the ensemble (host memory and its graph; members and workspaces stay). */
+void pic_ensemble_free(pic_ensemble* e);
+
 /* ---------------------------------------------------------------------------------------
  * Allocation-free field solve.  The paper has no counterpart: it is a deployment variant of
  * the field solve of §2 step 2 (exact discrete Green's function, reading C-23) for callers

@@ -271,9 +271,19 @@ cudaError_t launch_place(const pic_handle* h) {
 }
 }  // namespace
 
+namespace {
+// The last CUDA error a call of this thread turned into PIC_ERR_CUDA (pic_last_cuda_error).
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+void note_cuda(cudaError_t e) {
+  if (e != cudaSuccess) g_last_cuda = e;
+}
+}  // namespace
+
 #define PIC_CUDA(call)                        \
   do {                                        \
-    if ((call) != cudaSuccess) {              \
+    const cudaError_t pic_e_ = (call);        \
+    if (pic_e_ != cudaSuccess) {              \
+      note_cuda(pic_e_);                      \
       (void)cudaGetLastError();               \
       return PIC_ERR_CUDA;                    \
     }                                         \
@@ -393,7 +403,7 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   int dev = 0, sms = 0;
   cudaStream_t st = h->stream;
   auto fail = [&](int code) {
-    (void)cudaGetLastError();
+    note_cuda(cudaGetLastError());
     delete h;
     return code;
   };
@@ -457,7 +467,7 @@ int pic_step(pic_handle* h, int64_t n_steps) {
   if (!h || n_steps < 0) return PIC_ERR_PARAM;
   for (int64_t i = 0; i < n_steps; ++i) {
     if (launch_particles(h) != cudaSuccess || launch_place(h) != cudaSuccess) {
-      (void)cudaGetLastError();
+      note_cuda(cudaGetLastError());
       return PIC_ERR_CUDA;
     }
   }
@@ -470,7 +480,7 @@ int pic_step_profiled(pic_handle* h, int64_t n_steps, double* ms_out) {
   for (int k = 0; k < 3; ++k)
     if (cudaEventCreate(&ev[k]) != cudaSuccess) {
       for (int m = 0; m < k; ++m) cudaEventDestroy(ev[m]);
-      (void)cudaGetLastError();
+      note_cuda(cudaGetLastError());
       return PIC_ERR_CUDA;
     }
   int rc = PIC_OK;
@@ -492,7 +502,7 @@ int pic_step_profiled(pic_handle* h, int64_t n_steps, double* ms_out) {
   }
   for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
   if (rc != PIC_OK) {
-    (void)cudaGetLastError();
+    note_cuda(cudaGetLastError());
     return rc;
   }
   return h->last_status;
@@ -779,7 +789,240 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   return out->omega_pe_dt_max > 2.0 ? PIC_WARN_UNSTABLE : PIC_OK;
 }
 
+// ------------------------------------------------------------------- ensemble (§3 scans)
+}  // extern "C"
+
+struct pic_ensemble {
+  std::vector<pic_handle*> sims;
+  EnsDev* E = nullptr;  // in the caller's ensemble workspace
+  cudaStream_t stream = nullptr;
+  size_t smem = 0;
+  int sms = 0, max_bps = 0, bps = 0, unit = 2048;
+  bool want_graph = true, have_graph = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int last_status = PIC_OK;
+};
+
+namespace {
+
+void drop_graph(pic_ensemble* e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  e->exec = nullptr;
+  e->graph = nullptr;
+  e->have_graph = false;
+}
+
+// Record one step's launch as a CUDA graph (replayed by pic_ensemble_step); on any failure
+// the ensemble falls back to direct launches.
+void build_graph(pic_ensemble* e) {
+  drop_graph(e);
+  if (!e->want_graph) return;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    note_cuda(cudaGetLastError());
+    return;
+  }
+  const cudaError_t le = launch_ensemble(e->E, e->sms * e->bps, e->smem, e->stream);
+  const cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+  if (le != cudaSuccess || ce != cudaSuccess || !g) {
+    note_cuda(cudaGetLastError());
+    if (g) cudaGraphDestroy(g);
+    return;
+  }
+  cudaGraphExec_t x = nullptr;
+  if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+    note_cuda(cudaGetLastError());
+    cudaGraphDestroy(g);
+    return;
+  }
+  e->graph = g;
+  e->exec = x;
+  e->have_graph = true;
+}
+
+cudaError_t ensemble_launch(pic_ensemble* e) {
+  if (e->have_graph) return cudaGraphLaunch(e->exec, e->stream);
+  return launch_ensemble(e->E, e->sms * e->bps, e->smem, e->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+static_assert(PIC_MAX_ENSEMBLE == kMaxEnsemble, "header and device limits agree");
+
+int pic_ensemble_workspace_bytes(int n, size_t* bytes) {
+  if (n < 1 || n > kMaxEnsemble || !bytes) return PIC_ERR_PARAM;
+  *bytes = (sizeof(EnsDev) + 255) & ~size_t(255);
+  return PIC_OK;
+}
+
+int pic_ensemble_create(pic_handle* const* sims, int n, const int64_t* target_steps,
+                        void* workspace, size_t workspace_bytes, pic_ensemble** out) {
+  if (!out || !sims || !target_steps || n < 1 || n > kMaxEnsemble) return PIC_ERR_PARAM;
+  *out = nullptr;
+  size_t need = 0;
+  pic_ensemble_workspace_bytes(n, &need);
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return PIC_ERR_WORKSPACE;
+  int nx_max = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!sims[i] || sims[i]->p.precision != PIC_FP32 || sims[i]->stream != sims[0]->stream ||
+        target_steps[i] < 0)
+      return PIC_ERR_PARAM;
+    for (int j = 0; j < i; ++j)
+      if (sims[j] == sims[i]) return PIC_ERR_PARAM;
+    nx_max = std::max(nx_max, sims[i]->K.nx);
+  }
+  pic_ensemble* e = new (std::nothrow) pic_ensemble;
+  if (!e) return PIC_ERR_PARAM;
+  e->sims.assign(sims, sims + n);
+  e->stream = sims[0]->stream;
+  e->E = static_cast<EnsDev*>(workspace);
+  auto fail = [&](int code) {
+    note_cuda(cudaGetLastError());
+    delete e;
+    return code;
+  };
+  // shared memory: the particle phase's tables and pipes; the placement prefixes of one
+  // simulation are kept within the same room, which bounds its list owners
+  const size_t p1 = ensemble_smem_bytes(nx_max, 0);
+  const int gcap_lim = (int)(p1 / (5 * sizeof(int))) & ~3;
+  e->smem = ensemble_smem_bytes(nx_max, gcap_lim);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      configure_ensemble(e->smem) != cudaSuccess)
+    return fail(PIC_ERR_CUDA);
+  e->max_bps = std::min(ensemble_blocks_per_sm(e->smem), 2);
+  if (e->max_bps < 1 || e->sms * 1 <= n) return fail(PIC_ERR_PARAM);
+  e->bps = e->max_bps;
+  std::vector<char> hbuf(sizeof(EnsDev), 0);
+  EnsDev* h = reinterpret_cast<EnsDev*>(hbuf.data());
+  h->n = n;
+  h->unit = e->unit;
+  h->pipes_off = (int)ensemble_pipes_offset(nx_max);
+  for (int i = 0; i < n; ++i) {
+    const long long nl = max_list_blocks(sims[i]->p);
+    h->sims[i] = sims[i]->K.self;
+    h->st[i] = sims[i]->K.st;
+    h->target[i] = target_steps[i];
+    h->gcap[i] = (int)std::min<long long>(nl - 4, gcap_lim);
+    h->gstride[i] = (int)nl;
+  }
+  if (cudaMemcpyAsync(e->E, h, sizeof(EnsDev), cudaMemcpyHostToDevice, e->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(e->stream) != cudaSuccess)
+    return fail(PIC_ERR_CUDA);
+  build_graph(e);
+  *out = e;
+  return PIC_OK;
+}
+
+int pic_ensemble_configure(pic_ensemble* e, int32_t unit, int32_t blocks_per_sm,
+                           int32_t use_graph) {
+  if (!e || unit < 256 || unit > kMaxEnsUnit || blocks_per_sm < 1 || blocks_per_sm > e->max_bps)
+    return PIC_ERR_PARAM;
+  PIC_CUDA(cudaStreamSynchronize(e->stream));
+  e->unit = unit;
+  e->bps = blocks_per_sm;
+  e->want_graph = use_graph != 0;
+  PIC_CUDA(cudaMemcpy(&e->E->unit, &e->unit, sizeof(int), cudaMemcpyHostToDevice));
+  build_graph(e);
+  return PIC_OK;
+}
+
+int pic_ensemble_step(pic_ensemble* e, int64_t n_steps) {
+  if (!e || n_steps < 0) return PIC_ERR_PARAM;
+  for (int64_t i = 0; i < n_steps; ++i) PIC_CUDA(ensemble_launch(e));
+  return e->last_status;
+}
+
+int pic_ensemble_sync(pic_ensemble* e) {
+  if (!e) return PIC_ERR_PARAM;
+  PIC_CUDA(cudaStreamSynchronize(e->stream));
+  int st = 0;
+  PIC_CUDA(cudaMemcpy(&st, &e->E->status, sizeof st, cudaMemcpyDeviceToHost));
+  int code = status_code(st);  // the ensemble's own (barrier) status first
+  for (pic_handle* h : e->sims) {
+    const int c = pic_sync(h);
+    if (code == PIC_OK && c != PIC_OK) code = c;
+  }
+  e->last_status = code;
+  return code;
+}
+
+int pic_ensemble_autotune(pic_ensemble* e, int32_t trial_steps, int32_t* chosen) {
+  if (!e || trial_steps < 1) return PIC_ERR_PARAM;
+  const int32_t units[3] = {1024, 2048, 4000};
+  float best = 0.0f;
+  int32_t bu = e->unit, bb = e->bps;
+  cudaEvent_t a = nullptr, b = nullptr;
+  PIC_CUDA(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return PIC_ERR_CUDA;
+  }
+  int rc = PIC_OK;
+  for (int bps = 1; bps <= e->max_bps && rc == PIC_OK; ++bps)
+    for (int k = 0; k < 3 && rc == PIC_OK; ++k) {
+      rc = pic_ensemble_configure(e, units[k], bps, e->want_graph ? 1 : 0);
+      if (rc != PIC_OK) break;
+      float ms = 0.0f;
+      if (ensemble_launch(e) != cudaSuccess || cudaEventRecord(a, e->stream) != cudaSuccess) {
+        rc = PIC_ERR_CUDA;
+        break;
+      }
+      for (int t = 0; t < trial_steps && rc == PIC_OK; ++t)
+        if (ensemble_launch(e) != cudaSuccess) rc = PIC_ERR_CUDA;
+      if (rc != PIC_OK || cudaEventRecord(b, e->stream) != cudaSuccess ||
+          cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        rc = PIC_ERR_CUDA;
+        break;
+      }
+      if (best == 0.0f || ms < best) {
+        best = ms;
+        bu = units[k];
+        bb = bps;
+      }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != PIC_OK) {
+    note_cuda(cudaGetLastError());
+    return rc;
+  }
+  rc = pic_ensemble_configure(e, bu, bb, e->want_graph ? 1 : 0);
+  if (rc == PIC_OK && chosen) {
+    chosen[0] = bu;
+    chosen[1] = bb;
+  }
+  return rc;
+}
+
+int pic_ensemble_info(pic_ensemble* e, int32_t* out) {
+  if (!e || !out) return PIC_ERR_PARAM;
+  out[0] = e->unit;
+  out[1] = e->bps;
+  out[2] = e->sms * e->bps;
+  out[3] = e->have_graph ? 1 : 0;
+  out[4] = (int32_t)e->smem;
+  return PIC_OK;
+}
+
+void pic_ensemble_free(pic_ensemble* e) {
+  if (!e) return;
+  drop_graph(e);
+  delete e;
+}
+
 void pic_free(pic_handle* h) { delete h; }
+
+const char* pic_last_cuda_error(void) {
+  return g_last_cuda == cudaSuccess ? "no CUDA error" : cudaGetErrorString(g_last_cuda);
+}
 
 const char* pic_strerror(int code) {
   switch (code) {

@@ -21,6 +21,17 @@ __device__ __forceinline__ void chain_release() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Raise (never lower) a kernel's dynamic shared-memory limit: handles with different grids
+// share the kernel, and a limit set for a smaller grid must not break a larger one.
+template <typename... Args>
+cudaError_t raise_smem_limit(void (*kernel)(Args...), size_t bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <typename... Args>
 cudaError_t launch_chained(void (*kernel)(Args...), unsigned grid, unsigned block, size_t smem,
                            cudaStream_t s, Args... args) {

@@ -75,6 +75,29 @@ struct DevState {
   unsigned id_snap[2];           // next_id at the start of the current step's particle pass
 };
 
+// Device-side state of an ensemble of FP32 simulations advanced by one launch per step (the
+// paper's parameter scans, §3): the simulations' own contexts and states, and the few words
+// the launch shares between its blocks.
+constexpr int kMaxEnsemble = 128;
+constexpr int kMaxEnsUnit = 4000;  // particles per list owner: keeps the 32-bit counters safe
+struct DevCtx;
+struct EnsDev {
+  unsigned estep;      // launches so far (parity selects the totals buffer)
+  unsigned bar_count;  // grid barrier: arrivals of the current generation
+  unsigned bar_gen;    // grid barrier: generation
+  int status;          // kSt* bits of the ensemble (a barrier that timed out)
+  int n;               // simulations
+  int unit;            // particles (both species) per list owner, <= kMaxEnsUnit
+  int pipes_off;       // byte offset of the warps' staging pipes in dynamic shared memory
+  int pad;
+  const DevCtx* sims[kMaxEnsemble];  // each simulation's context (device copy)
+  DevState* st[kMaxEnsemble];        // each simulation's state
+  long long target[kMaxEnsemble];    // step index at which a simulation stops
+  int gcap[kMaxEnsemble];            // most list owners a simulation may use
+  int gstride[kMaxEnsemble];         // row stride of its five list-count arrays
+  int tot[2][kMaxEnsemble][5];       // list totals per simulation, by launch parity
+};
+
 // Everything a kernel needs, passed by value (constant bank).  Pointers address the
 // caller's workspace.
 struct DevCtx {

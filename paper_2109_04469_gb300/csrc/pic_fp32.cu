@@ -38,9 +38,11 @@ namespace pic {
 #endif
 
 constexpr int kWarps32 = kBlock / 32;
-constexpr int kRoundPerWarp = 4096;  // particles a warp handles between counter flushes
-// 8 warps x 4096 particles x (a particle + a birth) x 2^16 < 2^32: the 32-bit counters of a
-// block cannot overflow between flushes.
+constexpr int kRoundPerWarp = 4064;  // particles a warp handles between counter flushes
+// A counter takes at most two full weights per particle of the round (the particle and one
+// birth: an ionization electron, or an electron emitted at a wall node by an ion), so
+// 8 warps x 4064 particles x 2 x 2^16 < 2^32: the 32-bit counters of a block cannot overflow
+// between flushes.  4064 is a multiple of 32, so every round starts on a tile boundary.
 constexpr unsigned short kCdFlag = 0x8000;  // countdown expires without a candidate
 constexpr int kPurCount = 4;                 // stream purpose: countdown of a new particle
 
@@ -725,6 +727,236 @@ __global__ void k_deposit32(DevCtx K, int s, int buf, long long n) {
   atomicAdd(&C[j + 1], (unsigned long long)wr << 16);
 }
 
+// ------------------------------------------------------------ ensemble (one launch a step)
+// All blocks of the ensemble launch are resident together (cooperative launch), so they can
+// meet at a grid barrier; the wait is bounded and reports kStTimeout instead of hanging.
+constexpr long long kGridSpinLimit = 1ll << 22;  // polls, ~128 ns apart (~0.5 s)
+
+__device__ bool grid_barrier(EnsDev* E) {
+  __shared__ int sOk;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &E->bar_gen;
+    const unsigned g0 = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&E->bar_count, 1u) == gridDim.x - 1) {
+      E->bar_count = 0u;
+      __threadfence();
+      atomicAdd(&E->bar_gen, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g0 && it < kGridSpinLimit) {
+        __nanosleep(128);
+        ++it;
+      }
+      if (*gen == g0) {
+        ok = 0;
+        atomicOr(&E->status, kStTimeout);
+      }
+    }
+    __threadfence();
+    sOk = ok;
+  }
+  __syncthreads();
+  return sOk != 0;
+}
+
+// One step of every simulation of the ensemble that has not reached its target step.
+// Phase 1: the particle passes.  Each simulation's particles (both species) are cut into G_s
+// list owners of about E->unit particles; the owners of all simulations, laid end to end,
+// are split evenly over the blocks, and a block walks its owners simulation by simulation
+// with that simulation's tables in shared memory (one owner per warp per round).  The owners
+// play the role of the single-run warps: lists in particle order at the owner's first slot,
+// five counts per owner, and per-simulation totals by atomics.
+// Phase 2 (after the grid barrier): block s < n closes simulation s's step and solves its
+// next field; the other blocks split all simulations' births and tail moves evenly, forming
+// the list prefixes of each simulation they touch in shared memory.
+// Results do not depend on E->unit or on the grid: the compaction rule fixes every slot.
+__global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(EnsDev* E) {
+  extern __shared__ __align__(128) unsigned char esm[];
+  __shared__ long long sNe[kMaxEnsemble], sNi[kMaxEnsemble], sIt[kMaxEnsemble + 1];
+  __shared__ unsigned sStep[kMaxEnsemble];
+  __shared__ int sG[kMaxEnsemble], sU0[kMaxEnsemble + 1];
+  __shared__ unsigned long long sCnt[kNumCounters];
+  __shared__ CompactTot sT[2];
+  __shared__ unsigned sEstep;
+  const int n = E->n, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // phase 0: the step's owners of every simulation
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const DevState* st = E->st[s];
+    const unsigned step = st->step;
+    const long long ne = st->n[0], ni = st->n[1];
+    const bool active = (long long)step < E->target[s];
+    long long g = (ne + ni + E->unit - 1) / E->unit;
+    g = g < 1 ? 1 : (g > E->gcap[s] ? E->gcap[s] : g);
+    sNe[s] = ne;
+    sNi[s] = ni;
+    sStep[s] = step;
+    sG[s] = active ? (int)g : 0;
+    if (active && blockIdx.x == 0) snapshot_pass(*E->sims[s], step, ne, ni);
+  }
+  if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) sEstep = E->estep;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int s = 0; s < n; ++s) {
+      sU0[s] = run;
+      run += sG[s];
+    }
+    sU0[n] = run;
+  }
+  __syncthreads();
+  const unsigned par = sEstep & 1u;
+  // phase 1
+  {
+    const long long T = sU0[n];
+    const long long lo = T * blockIdx.x / gridDim.x, hi = T * (blockIdx.x + 1) / gridDim.x;
+    PipeCount Q{0u, 0u};
+    bool ok = true;
+    bool pipes_ready = false;
+    for (int s = 0; s < n && lo < hi; ++s) {
+      const long long ua = max(lo, (long long)sU0[s]) - sU0[s];
+      const long long ub = min(hi, (long long)sU0[s + 1]) - sU0[s];
+      if (ua >= ub) continue;
+      const DevCtx& K = *E->sims[s];
+      const int nx = K.nx;
+      float2* sE = reinterpret_cast<float2*>(esm);
+      unsigned* sC = reinterpret_cast<unsigned*>(sE + 2 * nx);
+      // the pipes sit after the largest tables of any simulation of the ensemble
+      WarpPipe& P = reinterpret_cast<WarpPipe*>(esm + (size_t)E->pipes_off)[warp];
+      if (!pipes_ready) {
+        if (lane == 0) {
+          for (int k = 0; k < kStages; ++k) mbar_init(&P.bar[k], 1u);
+          fence_mbar_init();
+        }
+        pipes_ready = true;
+      }
+      __syncthreads();  // the previous simulation's tables are no longer read
+      for (int sp = 0; sp < 2; ++sp)
+        for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+          const float a = K.fE[sp][j];
+          const float b = (j + 1 < nx) ? K.fE[sp][j + 1] : a;
+          sE[sp * nx + j] = make_float2(a, b - a);
+        }
+      for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0u;
+      __syncthreads();
+      const unsigned step = sStep[s];
+      const long long ne = sNe[s], ni = sNi[s];
+      const int G = sG[s], gs = E->gstride[s];
+      unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
+      for (long long base = ua; base < ub; base += kWarps32) {
+        const long long g = base + warp;
+        if (g < ub) {
+          // after a timed-out wait (status set) the warp's remaining owners list nothing
+          const long long q0 = range_begin(ne, (int)g, G), q1 = range_begin(ne, (int)g + 1, G);
+          long long hk = q0, ek = q0, ik = q0;
+          if (ok) ok = warp_pass32<0>(K, step, q0, q1, sE, sC, sC + nx, sCnt, P, Q, hk, ek, ik);
+          const int he = (int)(hk - q0), be0 = (int)(ek - q0), bi = (int)(ik - q0);
+          const long long r0 = range_begin(ni, (int)g, G), r1 = range_begin(ni, (int)g + 1, G);
+          hk = ek = ik = r0;
+          if (ok) ok = warp_pass32<1>(K, step, r0, r1, sE + nx, sC, sC + nx, sCnt, P, Q, hk, ek, ik);
+          const int hi_ = (int)(hk - r0), be1 = (int)(ek - r0);
+          if (lane == 0) {
+            int* rows = K.hole_cnt[0];
+            rows[g] = he;
+            rows[(size_t)gs + g] = hi_;
+            rows[2 * (size_t)gs + g] = be0;
+            rows[3 * (size_t)gs + g] = be1;
+            rows[4 * (size_t)gs + g] = bi;
+            int* t = E->tot[par][s];
+            if (he) atomicAdd(&t[0], he);
+            if (hi_) atomicAdd(&t[1], hi_);
+            if (be0) atomicAdd(&t[2], be0);
+            if (be1) atomicAdd(&t[3], be1);
+            if (bi) atomicAdd(&t[4], bi);
+          }
+        }
+        flush32(K, sC, Cn);  // one owner per warp per round: the counters stay in range
+      }
+      if (threadIdx.x < kNumCounters && sCnt[threadIdx.x]) {
+        atomicAdd(&K.counters[threadIdx.x], sCnt[threadIdx.x]);
+        sCnt[threadIdx.x] = 0ull;
+      }
+    }
+    if (pipes_ready) {
+      __syncwarp();
+      if (lane == 0) {
+        WarpPipe& P = reinterpret_cast<WarpPipe*>(esm + (size_t)E->pipes_off)[warp];
+        for (int k = 0; k < kStages; ++k) mbar_inval(&P.bar[k]);
+      }
+    }
+  }
+  if (!grid_barrier(E)) return;
+  // phase 2
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) E->estep = sEstep + 1u;
+    for (int i = threadIdx.x; i < n * 5; i += blockDim.x) E->tot[par ^ 1u][i / 5][i % 5] = 0;
+  }
+  // items of every simulation, from the totals
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    long long items = 0;
+    if (sG[s] > 0) {
+      const int* t = E->tot[par][s];
+      const long long cap = E->sims[s]->cap;
+      const long long N2[2] = {sNe[s], sNi[s]};
+      const long long H2[2] = {t[0], t[1]}, B2[2] = {(long long)t[2] + t[3], t[4]};
+      for (int sp = 0; sp < 2; ++sp) {
+        const long long limit = cap - (N2[sp] - H2[sp]);
+        const long long beff = B2[sp] < limit ? B2[sp] : limit;
+        const long long nn = N2[sp] - H2[sp] + beff;
+        items += beff + (H2[sp] > beff ? N2[sp] - nn : 0);
+      }
+    }
+    sIt[s] = items;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long run = 0;
+    for (int s = 0; s < n; ++s) {
+      const long long v = sIt[s];
+      sIt[s] = run;
+      run += v;
+    }
+    sIt[n] = run;
+  }
+  __syncthreads();
+  if ((int)blockIdx.x < n) {
+    const int s = blockIdx.x;
+    if (sG[s] > 0) {
+      const DevCtx& K = *E->sims[s];
+      if (threadIdx.x < 2) {
+        const int sp = threadIdx.x;
+        const int* t = E->tot[par][s];
+        CompactTot c;
+        c.N = sp ? sNi[s] : sNe[s];
+        c.H = t[sp];
+        c.B = sp ? t[4] : (long long)t[2] + t[3];
+        const long long limit = K.cap - (c.N - c.H);
+        c.Beff = c.B < limit ? c.B : limit;
+        c.Nn = c.N - c.H + c.Beff;
+        c.nid = K.st->id_snap[sp];
+        publish_counts(K, sp, c);
+      }
+      advance_field(K, esm);
+    }
+    return;
+  }
+  const int nb = gridDim.x - n, j = blockIdx.x - n;
+  const long long I = sIt[n];
+  const long long lo = I * j / nb, hi = I * (j + 1) / nb;
+  int* sp = reinterpret_cast<int*>(esm);
+  for (int s = 0; s < n && lo < hi; ++s) {
+    const long long a = max(lo, sIt[s]) - sIt[s], b = min(hi, sIt[s + 1]) - sIt[s];
+    if (a >= b) continue;
+    const DevCtx& K = *E->sims[s];
+    list_prefixes<kBlock>(K, sG[s], E->gstride[s], sp, sT);
+    place_items<Fp32Moves>(K, sG[s], sp, sT, a + threadIdx.x, b, (long long)blockDim.x);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------------ launchers
 size_t push32_smem_bytes(int nx) { return pipes_offset(nx) + sizeof(WarpPipe) * kWarps32; }
 
@@ -736,6 +968,40 @@ cudaError_t launch_push_fp32(const DevCtx& K, int grid, cudaStream_t s) {
 cudaError_t launch_place_fp32(const DevCtx& K, int grid, cudaStream_t s) {
   return launch_chained(k_place_field<Fp32Moves>, (unsigned)grid, 256u,
                         place_smem_bytes(K.nx, K.nlist), s, K);
+}
+
+size_t ensemble_pipes_offset(int nx_max) { return pipes_offset(nx_max); }
+size_t ensemble_smem_bytes(int nx_max, int gcap_max) {
+  const size_t p1 = pipes_offset(nx_max) + sizeof(WarpPipe) * kWarps32;
+  const size_t p2 = place_smem_bytes(nx_max, gcap_max);
+  return p1 > p2 ? p1 : p2;
+}
+
+cudaError_t configure_ensemble(size_t smem) {
+  return raise_smem_limit(k_ensemble_step, (int)smem);
+}
+
+int ensemble_blocks_per_sm(size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ensemble_step, kBlock, smem) !=
+      cudaSuccess)
+    return 0;
+  return nb;
+}
+
+// Cooperative launch: every block resident at once, so the grid barrier can complete.
+cudaError_t launch_ensemble(EnsDev* E, int grid, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)kBlock);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_ensemble_step, E);
 }
 
 cudaError_t launch_convert(const DevCtx& K, int species, long long n, bool to_fp32,
@@ -756,15 +1022,12 @@ cudaError_t launch_deposit32(const DevCtx& K, int species, int buf, long long n,
 }
 
 cudaError_t configure_kernels32(int nx) {
-  cudaError_t e = cudaFuncSetAttribute(k_push_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)push32_smem_bytes(nx));
+  cudaError_t e = raise_smem_limit(k_push_fp32, (int)push32_smem_bytes(nx));
   return e;
 }
 
 cudaError_t configure_place_fp32(int nx, int nlist) {
-  return cudaFuncSetAttribute(k_place_field<Fp32Moves>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)place_smem_bytes(nx, nlist));
+  return raise_smem_limit(k_place_field<Fp32Moves>, (int)place_smem_bytes(nx, nlist));
 }
 
 int push_fp32_blocks_per_sm(int nx) {

@@ -517,17 +517,13 @@ cudaError_t launch_max_abs(const double* v, long long n, unsigned long long* out
 }
 
 cudaError_t configure_kernels(int nx) {
-  cudaError_t e = cudaFuncSetAttribute(k_push_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)push_smem_bytes(nx));
+  cudaError_t e = raise_smem_limit(k_push_fp64, (int)push_smem_bytes(nx));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)field_smem_bytes(nx));
+  return raise_smem_limit(k_field, (int)field_smem_bytes(nx));
 }
 
 cudaError_t configure_place_fp64(int nx, int nlist) {
-  return cudaFuncSetAttribute(k_place_field<Fp64Moves>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)place_smem_bytes(nx, nlist));
+  return raise_smem_limit(k_place_field<Fp64Moves>, (int)place_smem_bytes(nx, nlist));
 }
 
 int push_fp64_blocks_per_sm(int nx) {

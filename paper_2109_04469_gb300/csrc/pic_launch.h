@@ -36,6 +36,12 @@ cudaError_t launch_convert(const DevCtx& K, int species, long long n, bool to_fp
 cudaError_t launch_deposit32(const DevCtx& K, int species, int buf, long long n, cudaStream_t s);
 cudaError_t configure_kernels32(int nx);
 cudaError_t configure_place_fp32(int nx, int nlist);
+// ensemble of FP32 simulations, one cooperative launch per step (pic_fp32.cu)
+size_t ensemble_pipes_offset(int nx_max);
+size_t ensemble_smem_bytes(int nx_max, int gcap_max);
+cudaError_t configure_ensemble(size_t smem);
+int ensemble_blocks_per_sm(size_t smem);
+cudaError_t launch_ensemble(EnsDev* E, int grid, size_t smem, cudaStream_t s);
 int push_fp32_blocks_per_sm(int nx);
 
 }  // namespace pic

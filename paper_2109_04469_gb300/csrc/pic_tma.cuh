@@ -22,6 +22,11 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned coun
                : "memory");
 }
 
+// retire a barrier before its shared memory is used for anything else
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // make barrier initialisation visible to the async (bulk-copy) proxy
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

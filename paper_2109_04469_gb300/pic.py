@@ -101,6 +101,15 @@ def lib() -> C.CDLL:
                 "pic_get_derived": (C.c_int, [P, P]),
                 "pic_free": (None, [P]),
                 "pic_strerror": (C.c_char_p, [C.c_int]),
+                "pic_last_cuda_error": (C.c_char_p, []),
+                "pic_ensemble_workspace_bytes": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
+                "pic_ensemble_create": (C.c_int, [P, C.c_int, P, P, C.c_size_t, C.POINTER(P)]),
+                "pic_ensemble_step": (C.c_int, [P, i64]),
+                "pic_ensemble_sync": (C.c_int, [P]),
+                "pic_ensemble_configure": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
+                "pic_ensemble_autotune": (C.c_int, [P, C.c_int32, P]),
+                "pic_ensemble_info": (C.c_int, [P, P]),
+                "pic_ensemble_free": (None, [P]),
                 "pic_field_solve_static": (C.c_int, [P, P, C.c_int32, C.c_double, C.c_double,
                                                      C.c_double, C.c_double, P, P, P]),
             }
@@ -116,6 +125,8 @@ class PicError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
         msg = lib().pic_strerror(code).decode() if _lib else ERRORS.get(code, str(code))
+        if _lib and code == -2:
+            msg += ": " + lib().pic_last_cuda_error().decode()
         super().__init__(f"{what}: {ERRORS.get(code, code)} ({msg})")
 
 
@@ -315,3 +326,61 @@ def field_solve_static(charge_e, charge_i, n_cells: int, gap_m: float, weight: f
         float(gap_m), float(weight), float(area_m2), float(v_left),
         C.c_void_p(phi.data_ptr()), C.c_void_p(efield.data_ptr()), C.c_void_p(s.cuda_stream)),
         "pic_field_solve_static")
+
+
+class Ensemble:
+    """PIC_FP32 simulations advanced together, one launch per step (pic_ensemble_*).
+
+    `sims` are Simulation objects on one stream; `targets[i]` is the step index at which
+    member i stops.  Members keep every single-run method (diag, particles, grid, ...)."""
+
+    def __init__(self, sims, targets):
+        import torch
+
+        self.sims = list(sims)
+        n = len(self.sims)
+        nb = C.c_size_t(0)
+        _check(lib().pic_ensemble_workspace_bytes(n, C.byref(nb)), "pic_ensemble_workspace_bytes")
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+        hs = (C.c_void_p * n)(*[s._h.value for s in self.sims])
+        tg = np.ascontiguousarray(targets, dtype=np.int64)
+        if tg.shape != (n,):
+            raise ValueError("one target step per member")
+        h = C.c_void_p()
+        _check(lib().pic_ensemble_create(hs, n, _ptr(tg), C.c_void_p(self.workspace.data_ptr()),
+                                         nb.value, C.byref(h)), "pic_ensemble_create")
+        self._h = h
+
+    def step(self, n: int = 1) -> int:
+        return _check(lib().pic_ensemble_step(self._h, int(n)), "pic_ensemble_step")
+
+    def sync(self) -> int:
+        return _check(lib().pic_ensemble_sync(self._h), "pic_ensemble_sync")
+
+    def configure(self, unit: int, blocks_per_sm: int, graph: bool = True):
+        _check(lib().pic_ensemble_configure(self._h, int(unit), int(blocks_per_sm), int(graph)),
+               "pic_ensemble_configure")
+
+    def autotune(self, trial_steps: int = 3) -> tuple[int, int]:
+        out = np.zeros(2, dtype=np.int32)
+        _check(lib().pic_ensemble_autotune(self._h, int(trial_steps), _ptr(out)),
+               "pic_ensemble_autotune")
+        return int(out[0]), int(out[1])
+
+    def info(self) -> dict:
+        out = np.zeros(5, dtype=np.int32)
+        _check(lib().pic_ensemble_info(self._h, _ptr(out)), "pic_ensemble_info")
+        return dict(zip(("unit", "blocks_per_sm", "grid", "graph", "smem_bytes"),
+                        (int(v) for v in out)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_ensemble_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
