@@ -912,6 +912,14 @@ int pic_ensemble_create(pic_handle* const* sims, int n, const int64_t* target_st
     h->gcap[i] = (int)std::min<long long>(nl - 4, gcap_lim);
     h->gstride[i] = (int)nl;
   }
+  // phase-1 order: members whose electrons are collision candidates most often (the costly
+  // particles) first, so the last chunks taken are cheap ones
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    return sims[a]->d.pmax[0] > sims[b]->d.pmax[0];
+  });
+  for (int i = 0; i < n; ++i) h->order[i] = ord[i];
   if (cudaMemcpyAsync(e->E, h, sizeof(EnsDev), cudaMemcpyHostToDevice, e->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(e->stream) != cudaSuccess)

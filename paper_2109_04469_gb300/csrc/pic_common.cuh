@@ -324,10 +324,23 @@ __device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, Comp
   const unsigned nid2[2] = {K.st->id_snap[0], K.st->id_snap[1]};
   if ((gstride & 3) == 0) {  // rows start on 16-byte boundaries: 16-byte loads, all in flight
     const int n4 = Gp / 4;
-    for (int i = threadIdx.x; i < kA * n4; i += NT) {
-      const int a = i / n4, c = i - a * n4;
-      reinterpret_cast<int4*>(sp + a * Gp)[c] =
-          __ldcg(reinterpret_cast<const int4*>(K.hole_cnt[0] + (size_t)a * gstride) + c);
+    for (int c0 = threadIdx.x; c0 < n4; c0 += 2 * NT) {
+      int4 v[kA][2];
+#pragma unroll
+      for (int a = 0; a < kA; ++a)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int c = c0 + u * NT;
+          if (c < n4)
+            v[a][u] = __ldcg(reinterpret_cast<const int4*>(K.hole_cnt[0] + (size_t)a * gstride) + c);
+        }
+#pragma unroll
+      for (int a = 0; a < kA; ++a)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int c = c0 + u * NT;
+          if (c < n4) reinterpret_cast<int4*>(sp + a * Gp)[c] = v[a][u];
+        }
     }
   } else {
     for (int i = threadIdx.x; i < kA * G; i += NT) {

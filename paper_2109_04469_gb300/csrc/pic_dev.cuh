@@ -96,6 +96,8 @@ struct EnsDev {
   int gcap[kMaxEnsemble];            // most list owners a simulation may use
   int gstride[kMaxEnsemble];         // row stride of its five list-count arrays
   int tot[2][kMaxEnsemble][5];       // list totals per simulation, by launch parity
+  int order[kMaxEnsemble];           // phase-1 order of the members: costliest first
+  unsigned next_chunk[2];            // phase-1 work counter, by launch parity
 };
 
 // Everything a kernel needs, passed by value (constant bank).  Pointers address the

@@ -764,9 +764,9 @@ __device__ bool grid_barrier(EnsDev* E) {
 
 // One step of every simulation of the ensemble that has not reached its target step.
 // Phase 1: the particle passes.  Each simulation's particles (both species) are cut into G_s
-// list owners of about E->unit particles; the owners of all simulations, laid end to end,
-// are split evenly over the blocks, and a block walks its owners simulation by simulation
-// with that simulation's tables in shared memory (one owner per warp per round).  The owners
+// list owners of about E->unit particles, grouped in chunks of one owner per warp; blocks
+// take chunks from a shared counter (members costliest first) and load a member's tables
+// into shared memory when their chunk changes member.  The owners
 // play the role of the single-run warps: lists in particle order at the owner's first slot,
 // five counts per owner, and per-simulation totals by atomics.
 // Phase 2 (after the grid barrier): block s < n closes simulation s's step and solves its
@@ -777,7 +777,8 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
   extern __shared__ __align__(128) unsigned char esm[];
   __shared__ long long sNe[kMaxEnsemble], sNi[kMaxEnsemble], sIt[kMaxEnsemble + 1];
   __shared__ unsigned sStep[kMaxEnsemble];
-  __shared__ int sG[kMaxEnsemble], sU0[kMaxEnsemble + 1];
+  __shared__ int sG[kMaxEnsemble], sC0[kMaxEnsemble + 1], sOrd[kMaxEnsemble];
+  __shared__ unsigned sChunk;
   __shared__ unsigned long long sCnt[kNumCounters];
   __shared__ CompactTot sT[2];
   __shared__ unsigned sEstep;
@@ -799,100 +800,110 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
   if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) sEstep = E->estep;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {  // chunks of kWarps32 owners (one round), members costliest first
     int run = 0;
-    for (int s = 0; s < n; ++s) {
-      sU0[s] = run;
-      run += sG[s];
+    for (int k = 0; k < n; ++k) {
+      const int s = E->order[k];
+      sOrd[k] = s;
+      sC0[k] = run;
+      run += (sG[s] + kWarps32 - 1) / kWarps32;
     }
-    sU0[n] = run;
+    sC0[n] = run;
   }
   __syncthreads();
   const unsigned par = sEstep & 1u;
-  // phase 1
+  // phase 1: blocks take chunks (one owner per warp) from a shared counter until none is left,
+  // so members whose particles cost more (more collision candidates) do not hold back a
+  // block that a static split would have given too much
   {
-    const long long T = sU0[n];
-    const long long lo = T * blockIdx.x / gridDim.x, hi = T * (blockIdx.x + 1) / gridDim.x;
+    const unsigned TC = (unsigned)sC0[n];
     PipeCount Q{0u, 0u};
     bool ok = true;
-    bool pipes_ready = false;
-    for (int s = 0; s < n && lo < hi; ++s) {
-      const long long ua = max(lo, (long long)sU0[s]) - sU0[s];
-      const long long ub = min(hi, (long long)sU0[s + 1]) - sU0[s];
-      if (ua >= ub) continue;
+    WarpPipe& P = reinterpret_cast<WarpPipe*>(esm + (size_t)E->pipes_off)[warp];
+    if (lane == 0) {
+      for (int k = 0; k < kStages; ++k) mbar_init(&P.bar[k], 1u);
+      fence_mbar_init();
+    }
+    int cur = -1;  // member (position in the order) whose tables are in shared memory
+    float2* sE = reinterpret_cast<float2*>(esm);
+    for (;;) {
+      if (threadIdx.x == 0) sChunk = atomicAdd(&E->next_chunk[par], 1u);
+      __syncthreads();
+      const unsigned c = sChunk;
+      if (c >= TC) break;
+      int k = 0;  // the member holding chunk c: last k with sC0[k] <= c
+      for (int lo2 = 0, hi2 = n; lo2 < hi2;) {
+        const int mid = (lo2 + hi2) >> 1;
+        if ((unsigned)sC0[mid] <= c) {
+          k = mid;
+          lo2 = mid + 1;
+        } else {
+          hi2 = mid;
+        }
+      }
+      const int s = sOrd[k];
       const DevCtx& K = *E->sims[s];
       const int nx = K.nx;
-      float2* sE = reinterpret_cast<float2*>(esm);
       unsigned* sC = reinterpret_cast<unsigned*>(sE + 2 * nx);
-      // the pipes sit after the largest tables of any simulation of the ensemble
-      WarpPipe& P = reinterpret_cast<WarpPipe*>(esm + (size_t)E->pipes_off)[warp];
-      if (!pipes_ready) {
-        if (lane == 0) {
-          for (int k = 0; k < kStages; ++k) mbar_init(&P.bar[k], 1u);
-          fence_mbar_init();
+      if (k != cur) {
+        if (cur >= 0 && threadIdx.x < kNumCounters && sCnt[threadIdx.x]) {
+          atomicAdd(&E->sims[sOrd[cur]]->counters[threadIdx.x], sCnt[threadIdx.x]);
+          sCnt[threadIdx.x] = 0ull;
         }
-        pipes_ready = true;
+        for (int sp = 0; sp < 2; ++sp)
+          for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+            const float a = K.fE[sp][j];
+            const float b = (j + 1 < nx) ? K.fE[sp][j + 1] : a;
+            sE[sp * nx + j] = make_float2(a, b - a);
+          }
+        for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0u;
+        cur = k;
+        __syncthreads();
       }
-      __syncthreads();  // the previous simulation's tables are no longer read
-      for (int sp = 0; sp < 2; ++sp)
-        for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-          const float a = K.fE[sp][j];
-          const float b = (j + 1 < nx) ? K.fE[sp][j + 1] : a;
-          sE[sp * nx + j] = make_float2(a, b - a);
-        }
-      for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0u;
-      __syncthreads();
       const unsigned step = sStep[s];
       const long long ne = sNe[s], ni = sNi[s];
       const int G = sG[s], gs = E->gstride[s];
       unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
-      for (long long base = ua; base < ub; base += kWarps32) {
-        const long long g = base + warp;
-        if (g < ub) {
-          // after a timed-out wait (status set) the warp's remaining owners list nothing
-          const long long q0 = range_begin(ne, (int)g, G), q1 = range_begin(ne, (int)g + 1, G);
-          long long hk = q0, ek = q0, ik = q0;
-          if (ok) ok = warp_pass32<0>(K, step, q0, q1, sE, sC, sC + nx, sCnt, P, Q, hk, ek, ik);
-          const int he = (int)(hk - q0), be0 = (int)(ek - q0), bi = (int)(ik - q0);
-          const long long r0 = range_begin(ni, (int)g, G), r1 = range_begin(ni, (int)g + 1, G);
-          hk = ek = ik = r0;
-          if (ok) ok = warp_pass32<1>(K, step, r0, r1, sE + nx, sC, sC + nx, sCnt, P, Q, hk, ek, ik);
-          const int hi_ = (int)(hk - r0), be1 = (int)(ek - r0);
-          if (lane == 0) {
-            int* rows = K.hole_cnt[0];
-            rows[g] = he;
-            rows[(size_t)gs + g] = hi_;
-            rows[2 * (size_t)gs + g] = be0;
-            rows[3 * (size_t)gs + g] = be1;
-            rows[4 * (size_t)gs + g] = bi;
-            int* t = E->tot[par][s];
-            if (he) atomicAdd(&t[0], he);
-            if (hi_) atomicAdd(&t[1], hi_);
-            if (be0) atomicAdd(&t[2], be0);
-            if (be1) atomicAdd(&t[3], be1);
-            if (bi) atomicAdd(&t[4], bi);
-          }
+      const long long g = (long long)(c - (unsigned)sC0[k]) * kWarps32 + warp;
+      if (g < G) {
+        // after a timed-out wait (status set) the warp's remaining owners list nothing
+        const long long q0 = range_begin(ne, (int)g, G), q1 = range_begin(ne, (int)g + 1, G);
+        long long hk = q0, ek = q0, ik = q0;
+        if (ok) ok = warp_pass32<0>(K, step, q0, q1, sE, sC, sC + nx, sCnt, P, Q, hk, ek, ik);
+        const int he = (int)(hk - q0), be0 = (int)(ek - q0), bi = (int)(ik - q0);
+        const long long r0 = range_begin(ni, (int)g, G), r1 = range_begin(ni, (int)g + 1, G);
+        hk = ek = ik = r0;
+        if (ok) ok = warp_pass32<1>(K, step, r0, r1, sE + nx, sC, sC + nx, sCnt, P, Q, hk, ek, ik);
+        const int hi_ = (int)(hk - r0), be1 = (int)(ek - r0);
+        if (lane == 0) {
+          int* rows = K.hole_cnt[0];
+          rows[g] = he;
+          rows[(size_t)gs + g] = hi_;
+          rows[2 * (size_t)gs + g] = be0;
+          rows[3 * (size_t)gs + g] = be1;
+          rows[4 * (size_t)gs + g] = bi;
+          int* t = E->tot[par][s];
+          if (he) atomicAdd(&t[0], he);
+          if (hi_) atomicAdd(&t[1], hi_);
+          if (be0) atomicAdd(&t[2], be0);
+          if (be1) atomicAdd(&t[3], be1);
+          if (bi) atomicAdd(&t[4], bi);
         }
-        flush32(K, sC, Cn);  // one owner per warp per round: the counters stay in range
       }
-      if (threadIdx.x < kNumCounters && sCnt[threadIdx.x]) {
-        atomicAdd(&K.counters[threadIdx.x], sCnt[threadIdx.x]);
-        sCnt[threadIdx.x] = 0ull;
-      }
+      flush32(K, sC, Cn);  // one owner per warp per chunk: the counters stay in range
     }
-    if (pipes_ready) {
-      __syncwarp();
-      if (lane == 0) {
-        WarpPipe& P = reinterpret_cast<WarpPipe*>(esm + (size_t)E->pipes_off)[warp];
-        for (int k = 0; k < kStages; ++k) mbar_inval(&P.bar[k]);
-      }
-    }
+    if (cur >= 0 && threadIdx.x < kNumCounters && sCnt[threadIdx.x])
+      atomicAdd(&E->sims[sOrd[cur]]->counters[threadIdx.x], sCnt[threadIdx.x]);
+    __syncwarp();
+    if (lane == 0)
+      for (int k = 0; k < kStages; ++k) mbar_inval(&P.bar[k]);
   }
   if (!grid_barrier(E)) return;
   // phase 2
   if (blockIdx.x == 0) {
     if (threadIdx.x == 0) E->estep = sEstep + 1u;
     for (int i = threadIdx.x; i < n * 5; i += blockDim.x) E->tot[par ^ 1u][i / 5][i % 5] = 0;
+    if (threadIdx.x == 0) E->next_chunk[par ^ 1u] = 0u;
   }
   // items of every simulation, from the totals
   for (int s = threadIdx.x; s < n; s += blockDim.x) {

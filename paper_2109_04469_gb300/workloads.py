@@ -49,3 +49,36 @@ def params(name: str, **overrides) -> dict:
     d.pop("rf_cycles", None)
     d.update(overrides)
     return d
+
+
+def ensemble_members(n: int = 64, seed: int = 2109, rf_cycles: float = 2.0,
+                     per_run=(2.5e5, 4.0e6)) -> list[tuple[dict, int]]:
+    """A parameter scan in the manner of §3: n uneven FP32 simulations on a Latin hypercube
+    over pressure 1-20 Pa (log), voltage 100-500 V, N_t 500-4000 (log), cells 100-800 (log),
+    weight giving `per_run` superparticles per simulation (both species, log; a 16x spread at
+    the default), R 0-0.7 and gamma 0-0.4.  2.5 cm gap, initial density 1e15 m^-3.  Each entry
+    is (parameters, target step index = rf_cycles x N_t): the members run uneven step
+    counts."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    d = 7
+    # Latin hypercube: one stratum per member and dimension, strata shuffled per dimension
+    u = (np.argsort(rng.random((d, n)), axis=1) + rng.random((d, n))) / n
+
+    def logu(x, a, b):
+        return float(np.exp(np.log(a) + x * (np.log(b) - np.log(a))))
+
+    out = []
+    gap, dens, area = 0.025, 1e15, COMMON["area_m2"]
+    for i in range(n):
+        nt = int(round(logu(u[2, i], 500, 4000)))
+        cells = int(round(logu(u[3, i], 100, 800)))
+        per_species = int(logu(u[4, i], per_run[0], per_run[1]) / 2)
+        c = dict(COMMON, gap_m=gap, pressure_pa=logu(u[0, i], 1.0, 20.0),
+                 v_rf_amp_v=100.0 + 400.0 * float(u[1, i]), steps_per_rf=nt, n_cells=cells,
+                 weight=dens * area * gap / per_species, refl_e=0.7 * float(u[5, i]),
+                 gamma_see=0.4 * float(u[6, i]), init_per_species=per_species,
+                 capacity_per_species=int(per_species * 3) + 4096, instance=i)
+        out.append((c, int(rf_cycles * nt)))
+    return out
