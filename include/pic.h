@@ -188,6 +188,30 @@ const char* pic_strerror(int code);
 const char* pic_last_cuda_error(void);
 
 /* ---------------------------------------------------------------------------------------
+ * Checkpoint / resume.  The paper's runs converge over thousands of RF periods (§3); a
+ * checkpoint holds the whole simulation state at a step boundary -- each species' particles
+ * in the handle's own representation, charge counts, field, accumulators, EEPF, FEDFs,
+ * counters, ids, step index and status -- so a handle resumed from it continues bit for bit
+ * as the saved one would have.  Collision tables are not saved: they follow from the
+ * parameters (a table replaced with pic_override_table must be replaced again).
+ * --------------------------------------------------------------------------------------- */
+
+/* Size in bytes of a checkpoint of the current state (it grows with the particle counts).
+ * Synchronises. */
+int pic_checkpoint_bytes(pic_handle* h, size_t* bytes);
+
+/* Write the current state into the caller's HOST buffer of >= pic_checkpoint_bytes bytes
+ * (a self-describing blob: magic "PICCKPT1", version, the parameters, then the arrays).
+ * Synchronises.  PIC_ERR_PARAM if the buffer is too small. */
+int pic_checkpoint_save(pic_handle* h, void* buffer, size_t bytes);
+
+/* Replace the handle's state by a checkpoint.  The handle must have been made with the same
+ * parameters (the initial load size and the capacity may differ; the capacity must hold the
+ * saved counts).  Synchronises.  PIC_ERR_PARAM for a foreign, damaged or truncated blob or
+ * other parameters; the handle is unchanged then. */
+int pic_checkpoint_load(pic_handle* h, const void* buffer, size_t bytes);
+
+/* ---------------------------------------------------------------------------------------
  * Ensembles: the paper's parameter scans (§3 varies N_t, N_x, W, R and γ around its base
  * cases) as many independent FP32 simulations advanced together, one cooperative launch per
  * step (replayed from a CUDA graph).  Each member is an ordinary PIC_FP32 handle made by

@@ -789,6 +789,167 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   return out->omega_pe_dt_max > 2.0 ? PIC_WARN_UNSTABLE : PIC_OK;
 }
 
+// ------------------------------------------------------------ checkpoint / resume (NEXT-4)
+}  // extern "C"
+
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  pic_params p;
+  int64_t n[2];
+  uint32_t next_id[2];
+  uint32_t step;
+  int32_t status;
+  int64_t steps_avg;
+  uint64_t payload_bytes;
+};
+
+struct Seg {
+  void* dev;
+  size_t bytes;
+};
+
+// The device arrays a checkpoint holds, in file order, for counts n[2]: each species'
+// particles in the handle's own representation (so a resumed run is bit for bit the same),
+// then the charge counts of both parity buffers, the field, the kick table (FP32), the
+// accumulators, EEPF, FEDFs and counters.
+std::vector<Seg> ckpt_segments(const pic_handle* h, const int64_t n[2]) {
+  const DevCtx& K = h->K;
+  std::vector<Seg> v;
+  for (int s = 0; s < 2; ++s) {
+    const size_t m = (size_t)n[s];
+    if (is_fp32(h)) {
+      v.push_back({K.ccd[s], 4 * m});
+      v.push_back({K.ov[s], 8 * m});
+      v.push_back({K.fvy[s], 4 * m});
+      v.push_back({K.fvz[s], 4 * m});
+    } else {
+      v.push_back({K.x[s], 8 * m});
+      v.push_back({K.vx[s], 8 * m});
+      v.push_back({K.vy[s], 8 * m});
+      v.push_back({K.vz[s], 8 * m});
+    }
+    v.push_back({K.id[s], 4 * m});
+  }
+  const size_t nx = (size_t)K.nx;
+  v.push_back({K.C, 8 * 4 * nx});
+  v.push_back({K.phi, 8 * nx});
+  v.push_back({K.E, 8 * nx});
+  if (is_fp32(h)) {
+    v.push_back({K.fE[0], 4 * nx});
+    v.push_back({K.fE[1], 4 * nx});
+  }
+  v.push_back({K.acc, 8 * 2 * nx});
+  v.push_back({K.eepf, 8 * (size_t)K.eepf_bins});
+  v.push_back({K.fedf, 8 * 2 * (size_t)K.fedf_bins});
+  v.push_back({K.counters, 8 * (size_t)kNumCounters});
+  return v;
+}
+
+size_t ckpt_payload(const std::vector<Seg>& v) {
+  size_t b = 0;
+  for (const Seg& s : v) b += s.bytes;
+  return b;
+}
+
+// Everything but the initial load size and the capacity must agree for a resume.
+bool same_physics(const pic_params& a, const pic_params& b) {
+  return a.gap_m == b.gap_m && a.pressure_pa == b.pressure_pa &&
+         a.gas_temp_k == b.gas_temp_k && a.v_rf_amp_v == b.v_rf_amp_v &&
+         a.f_rf_hz == b.f_rf_hz && a.steps_per_rf == b.steps_per_rf &&
+         a.n_cells == b.n_cells && a.weight == b.weight && a.refl_e == b.refl_e &&
+         a.gamma_see == b.gamma_see && a.area_m2 == b.area_m2 && a.init_te_ev == b.init_te_ev &&
+         a.see_energy_ev == b.see_energy_ev && a.seed == b.seed && a.instance == b.instance &&
+         a.precision == b.precision && a.eepf_bins == b.eepf_bins &&
+         a.eepf_emax_ev == b.eepf_emax_ev && a.fedf_bins == b.fedf_bins &&
+         a.fedf_emax_ev == b.fedf_emax_ev;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_checkpoint_bytes(pic_handle* h, size_t* bytes) {
+  if (!h || !bytes) return PIC_ERR_PARAM;
+  DevState s;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy(&s, h->K.st, sizeof s, cudaMemcpyDeviceToHost));
+  const int64_t n[2] = {s.n[0], s.n[1]};
+  *bytes = sizeof(CkptHeader) + ckpt_payload(ckpt_segments(h, n));
+  return PIC_OK;
+}
+
+int pic_checkpoint_save(pic_handle* h, void* buffer, size_t bytes) {
+  if (!h || !buffer) return PIC_ERR_PARAM;
+  DevState s;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  PIC_CUDA(cudaMemcpy(&s, h->K.st, sizeof s, cudaMemcpyDeviceToHost));
+  const int64_t n[2] = {s.n[0], s.n[1]};
+  const std::vector<Seg> segs = ckpt_segments(h, n);
+  const size_t payload = ckpt_payload(segs);
+  if (bytes < sizeof(CkptHeader) + payload) return PIC_ERR_PARAM;
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof hd);
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = kCkptVersion;
+  hd.header_bytes = sizeof(CkptHeader);
+  hd.p = h->p;
+  hd.n[0] = n[0];
+  hd.n[1] = n[1];
+  hd.next_id[0] = s.next_id[0];
+  hd.next_id[1] = s.next_id[1];
+  hd.step = s.step;
+  hd.status = s.status;
+  hd.steps_avg = s.steps_avg;
+  hd.payload_bytes = payload;
+  char* out = static_cast<char*>(buffer);
+  std::memcpy(out, &hd, sizeof hd);
+  size_t off = sizeof hd;
+  for (const Seg& g : segs) {
+    if (g.bytes) PIC_CUDA(cudaMemcpy(out + off, g.dev, g.bytes, cudaMemcpyDeviceToHost));
+    off += g.bytes;
+  }
+  return PIC_OK;
+}
+
+int pic_checkpoint_load(pic_handle* h, const void* buffer, size_t bytes) {
+  if (!h || !buffer || bytes < sizeof(CkptHeader)) return PIC_ERR_PARAM;
+  CkptHeader hd;
+  std::memcpy(&hd, buffer, sizeof hd);
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion ||
+      hd.header_bytes != sizeof(CkptHeader) || !same_physics(hd.p, h->p))
+    return PIC_ERR_PARAM;
+  const int64_t cap = h->p.capacity_per_species;
+  if (hd.n[0] < 0 || hd.n[1] < 0 || hd.n[0] > cap || hd.n[1] > cap) return PIC_ERR_PARAM;
+  const std::vector<Seg> segs = ckpt_segments(h, hd.n);
+  const size_t payload = ckpt_payload(segs);
+  if (hd.payload_bytes != payload || bytes < sizeof(CkptHeader) + payload) return PIC_ERR_PARAM;
+  PIC_CUDA(cudaStreamSynchronize(h->stream));
+  const char* in = static_cast<const char*>(buffer);
+  size_t off = sizeof hd;
+  for (const Seg& g : segs) {
+    if (g.bytes) PIC_CUDA(cudaMemcpy(g.dev, in + off, g.bytes, cudaMemcpyHostToDevice));
+    off += g.bytes;
+  }
+  DevState s;
+  PIC_CUDA(cudaMemcpy(&s, h->K.st, sizeof s, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 2; ++k) {
+    s.n[k] = s.n_snap[k] = hd.n[k];
+    s.next_id[k] = s.id_snap[k] = hd.next_id[k];
+  }
+  s.step = s.step_next = hd.step;
+  s.status = hd.status;
+  s.steps_avg = hd.steps_avg;
+  PIC_CUDA(cudaMemcpy(h->K.st, &s, sizeof s, cudaMemcpyHostToDevice));
+  h->last_status = status_code(hd.status);
+  return PIC_OK;
+}
+
 // ------------------------------------------------------------------- ensemble (§3 scans)
 }  // extern "C"
 

@@ -102,6 +102,9 @@ def lib() -> C.CDLL:
                 "pic_free": (None, [P]),
                 "pic_strerror": (C.c_char_p, [C.c_int]),
                 "pic_last_cuda_error": (C.c_char_p, []),
+                "pic_checkpoint_bytes": (C.c_int, [P, C.POINTER(C.c_size_t)]),
+                "pic_checkpoint_save": (C.c_int, [P, P, C.c_size_t]),
+                "pic_checkpoint_load": (C.c_int, [P, P, C.c_size_t]),
                 "pic_ensemble_workspace_bytes": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
                 "pic_ensemble_create": (C.c_int, [P, C.c_int, P, P, C.c_size_t, C.POINTER(P)]),
                 "pic_ensemble_step": (C.c_int, [P, i64]),
@@ -212,6 +215,19 @@ class Simulation:
         a, b = C.c_int64(), C.c_int64()
         _check(lib().pic_counts(self._h, C.byref(a), C.byref(b)), "pic_counts")
         return a.value, b.value
+
+    def checkpoint(self) -> np.ndarray:
+        """The whole state at the current step boundary, as a host byte array."""
+        nb = C.c_size_t(0)
+        _check(lib().pic_checkpoint_bytes(self._h, C.byref(nb)), "pic_checkpoint_bytes")
+        buf = np.zeros(nb.value, dtype=np.uint8)
+        _check(lib().pic_checkpoint_save(self._h, _ptr(buf), nb.value), "pic_checkpoint_save")
+        return buf
+
+    def restore(self, buf: np.ndarray) -> None:
+        """Resume from a checkpoint of a simulation with the same parameters."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().pic_checkpoint_load(self._h, _ptr(buf), buf.nbytes), "pic_checkpoint_load")
 
     def counts_async(self, out) -> None:
         """Enqueue a copy of the two counts into `out` (a pinned host int64 tensor of 2)."""
