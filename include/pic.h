@@ -262,6 +262,17 @@ int pic_ensemble_info(pic_ensemble* e, int32_t* out);
 void pic_ensemble_free(pic_ensemble* e);
 
 /* ---------------------------------------------------------------------------------------
+ * Surrogate network (the paper has none): BF16 tensor-core kernels.
+ * --------------------------------------------------------------------------------------- */
+
+/* C[m x n] = A[m x k] * B[n x k]^T on the tcgen05 tensor cores: A, B DEVICE arrays of BF16
+ * (raw 16-bit patterns), row-major with k contiguous; C a DEVICE FP32 array, row-major.
+ * FP32 accumulation.  m % 128 == 0, n % 16 == 0 with 16 <= n <= 256, k % 16 == 0, k >= 16
+ * (PIC_ERR_PARAM otherwise).  Synchronises; PIC_ERR_TIMEOUT if the MMAs never completed. */
+int pic_tc_gemm_bf16(const uint16_t* a, const uint16_t* b, float* c, int32_t m, int32_t n,
+                     int32_t k, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
  * Allocation-free field solve.  The paper has no counterpart: it is a deployment variant of
  * the field solve of §2 step 2 (exact discrete Green's function, reading C-23) for callers
  * that cannot allocate device memory -- code recorded into a CUDA graph by stream capture,

@@ -25,6 +25,8 @@ UNITS = {
     "pic_fp32.cu": [],
     # allocation-free field solve: same rounded FP64 operations as the FP64 path
     "pic_static.cu": ["-fmad=false"],
+    # surrogate network: tcgen05 BF16 GEMMs and FP32 elementwise kernels
+    "pic_mlp.cu": [],
 }
 
 

@@ -102,6 +102,7 @@ def lib() -> C.CDLL:
                 "pic_free": (None, [P]),
                 "pic_strerror": (C.c_char_p, [C.c_int]),
                 "pic_last_cuda_error": (C.c_char_p, []),
+                "pic_tc_gemm_bf16": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_int32, P]),
                 "pic_checkpoint_bytes": (C.c_int, [P, C.POINTER(C.c_size_t)]),
                 "pic_checkpoint_save": (C.c_int, [P, P, C.c_size_t]),
                 "pic_checkpoint_load": (C.c_int, [P, P, C.c_size_t]),
@@ -399,4 +400,21 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+def tc_gemm_bf16(a, b, c, stream=None) -> int:
+    """pic_tc_gemm_bf16 on CUDA tensors: a [m, k] and b [n, k] torch.bfloat16, c [m, n]
+    torch.float32 (all contiguous); c = a @ b.T with FP32 accumulation."""
+    import torch
+
+    m, k = a.shape
+    n = b.shape[0]
+    if (a.dtype != torch.bfloat16 or b.dtype != torch.bfloat16 or c.dtype != torch.float32
+            or b.shape[1] != k or tuple(c.shape) != (m, n)
+            or not all(t.is_cuda and t.is_contiguous() for t in (a, b, c))):
+        raise ValueError("tc_gemm_bf16: contiguous CUDA bf16 a[m,k], b[n,k] and fp32 c[m,n]")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _check(lib().pic_tc_gemm_bf16(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                                         C.c_void_p(c.data_ptr()), m, n, k,
+                                         C.c_void_p(s.cuda_stream)), "pic_tc_gemm_bf16")
 
