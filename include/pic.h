@@ -272,6 +272,36 @@ void pic_ensemble_free(pic_ensemble* e);
 int pic_tc_gemm_bf16(const uint16_t* a, const uint16_t* b, float* c, int32_t m, int32_t n,
                      int32_t k, void* cuda_stream);
 
+/* The network: inputs x[7] (pressure, voltage, dt, dx, weight, R, gamma, as the caller
+ * normalises them), two hidden layers of 256 with GELU (tanh form), 192 linear outputs (a
+ * 128-point density profile and a 64-bin log EEPF).  FP32 master parameters, BF16 copies
+ * for the tensor-core GEMMs, BF16 activations, FP32 accumulation, Adam (0.9, 0.999, 1e-8),
+ * mean-squared-error loss.  Flat parameter layout (pic_mlp_num_params() floats):
+ * W1[256][7], b1[256], W2[256][256], b2[256], W3[192][256], b3[192].  The caller owns one
+ * DEVICE workspace (pic_mlp_workspace_bytes, 256-byte aligned) sized for batches of up to
+ * batch_max (a multiple of 128) rows; all x / t / y arrays below are DEVICE arrays, row-major. */
+typedef struct pic_mlp pic_mlp;
+int pic_mlp_num_params(void);
+int pic_mlp_workspace_bytes(int32_t batch_max, size_t* bytes);
+/* Uniform initialisation (bound sqrt(6 / (fan_in + fan_out)), biases 0) from seed.
+ * Synchronises. */
+int pic_mlp_init(int32_t batch_max, uint64_t seed, void* workspace, size_t workspace_bytes,
+                 void* cuda_stream, pic_mlp** out);
+/* HOST arrays of pic_mlp_num_params() floats; set also clears the Adam state.  Synchronise. */
+int pic_mlp_get_params(pic_mlp* m, float* params);
+int pic_mlp_set_params(pic_mlp* m, const float* params);
+/* y[n][192] = network(x[n][7]), 1 <= n <= batch_max.  Enqueued. */
+int pic_mlp_forward(pic_mlp* m, const float* x, int32_t n, float* y);
+/* Loss and the gradient of the mean-squared error of targets t[n][192] with respect to every
+ * parameter (HOST array, flat layout), without updating; n % 128 == 0.  Synchronises. */
+int pic_mlp_gradients(pic_mlp* m, const float* x, const float* t, int32_t n, float* grads,
+                      float* loss);
+/* One Adam step with learning rate lr on a batch (n % 128 == 0).  If loss is not NULL, the
+ * batch's loss before the step is returned (synchronises); otherwise only enqueued. */
+int pic_mlp_train_step(pic_mlp* m, const float* x, const float* t, int32_t n, float lr,
+                       float* loss);
+void pic_mlp_free(pic_mlp* m);
+
 /* ---------------------------------------------------------------------------------------
  * Allocation-free field solve.  The paper has no counterpart: it is a deployment variant of
  * the field solve of §2 step 2 (exact discrete Green's function, reading C-23) for callers

@@ -103,6 +103,15 @@ def lib() -> C.CDLL:
                 "pic_strerror": (C.c_char_p, [C.c_int]),
                 "pic_last_cuda_error": (C.c_char_p, []),
                 "pic_tc_gemm_bf16": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_int32, P]),
+                "pic_mlp_num_params": (C.c_int, []),
+                "pic_mlp_workspace_bytes": (C.c_int, [C.c_int32, C.POINTER(C.c_size_t)]),
+                "pic_mlp_init": (C.c_int, [C.c_int32, C.c_uint64, P, C.c_size_t, P, C.POINTER(P)]),
+                "pic_mlp_get_params": (C.c_int, [P, P]),
+                "pic_mlp_set_params": (C.c_int, [P, P]),
+                "pic_mlp_forward": (C.c_int, [P, P, C.c_int32, P]),
+                "pic_mlp_gradients": (C.c_int, [P, P, P, C.c_int32, P, C.POINTER(C.c_float)]),
+                "pic_mlp_train_step": (C.c_int, [P, P, P, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
+                "pic_mlp_free": (None, [P]),
                 "pic_checkpoint_bytes": (C.c_int, [P, C.POINTER(C.c_size_t)]),
                 "pic_checkpoint_save": (C.c_int, [P, P, C.c_size_t]),
                 "pic_checkpoint_load": (C.c_int, [P, P, C.c_size_t]),
@@ -417,4 +426,76 @@ def tc_gemm_bf16(a, b, c, stream=None) -> int:
     return _check(lib().pic_tc_gemm_bf16(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
                                          C.c_void_p(c.data_ptr()), m, n, k,
                                          C.c_void_p(s.cuda_stream)), "pic_tc_gemm_bf16")
+
+
+class Mlp:
+    """The surrogate network on the library's tensor-core kernels (pic_mlp_*): x [n, 7] ->
+    y [n, 192]; CUDA float32 tensors in, out."""
+
+    def __init__(self, batch_max: int = 1024, seed: int = 1, stream=None):
+        import torch
+
+        nb = C.c_size_t(0)
+        _check(lib().pic_mlp_workspace_bytes(batch_max, C.byref(nb)), "pic_mlp_workspace_bytes")
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.batch_max = batch_max
+        self.n_params = lib().pic_mlp_num_params()
+        h = C.c_void_p()
+        _check(lib().pic_mlp_init(batch_max, seed, C.c_void_p(self.workspace.data_ptr()),
+                                  nb.value, C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+               "pic_mlp_init")
+        self._h = h
+
+    @staticmethod
+    def _dev(t, cols):
+        import torch
+
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[-1] != cols:
+            raise ValueError(f"contiguous CUDA float32 tensor [n, {cols}] expected")
+        return C.c_void_p(t.data_ptr())
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().pic_mlp_get_params(self._h, _ptr(out)), "pic_mlp_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.shape == (self.n_params,)
+        _check(lib().pic_mlp_set_params(self._h, _ptr(p)), "pic_mlp_set_params")
+
+    def forward(self, x):
+        import torch
+
+        n = x.shape[0]
+        y = torch.empty((n, 192), dtype=torch.float32, device="cuda")
+        _check(lib().pic_mlp_forward(self._h, self._dev(x, 7), n, self._dev(y, 192)),
+               "pic_mlp_forward")
+        return y
+
+    def gradients(self, x, t) -> tuple[np.ndarray, float]:
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_float(0.0)
+        _check(lib().pic_mlp_gradients(self._h, self._dev(x, 7), self._dev(t, 192), x.shape[0],
+                                       _ptr(g), C.byref(loss)), "pic_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, x, t, lr: float, want_loss: bool = True):
+        loss = C.c_float(0.0)
+        _check(lib().pic_mlp_train_step(self._h, self._dev(x, 7), self._dev(t, 192), x.shape[0],
+                                        float(lr), C.byref(loss) if want_loss else None),
+               "pic_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
