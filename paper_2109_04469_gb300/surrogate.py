@@ -1,0 +1,197 @@
+"""Surrogate of the parameter scans: a 7 -> 256 -> 256 -> 192 network,
+trained on the ensemble's own outputs, that maps a setting (pressure, voltage, time step,
+grid spacing, weight, R, gamma) to the RF-averaged electron density profile (128 points over
+x/L) and the centre EEPF (64 bins), and flags the settings that would break the accuracy
+criteria the paper revisits (§3.5: omega_pe dt <= 0.2, P_coll <= 0.05, dx <= lambda_D).
+
+Every step runs on the library: the scan as pic_ensemble launches, the network as the
+tensor-core kernels of pic_mlp_*.  The plain PIC/MCC is the fallback and the judge: it
+produces the training data and the held-out profiles the network is scored against.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import pic, workloads
+
+N_PROFILE, N_EEPF = 128, 64
+EEPF_EMAX = 30.0
+N_FLOOR = 1e12  # m^-3, floor of the log density (sheaths)
+F_FLOOR = 1e-6  # eV^-3/2, floor of the log EEPF
+QE, ME, EPS0 = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
+
+
+def sample_settings(n: int, seed: int = 7, per_species=(8e3, 3.2e4)) -> list[dict]:
+    """n settings on a Latin hypercube over the scan ranges of the batched workload (p 1-20 Pa,
+    V 100-500 V, N_t 500-4000, 100-800 cells, R 0-0.7, gamma 0-0.4) with small populations
+    (a 4x weight range) so that a scan of many settings runs in seconds."""
+    rng = np.random.default_rng(seed)
+    d = 7
+    u = (np.argsort(rng.random((d, n)), axis=1) + rng.random((d, n))) / n
+
+    def logu(x, a, b):
+        return float(np.exp(np.log(a) + x * (np.log(b) - np.log(a))))
+
+    out = []
+    gap, dens, area = 0.025, 1e15, workloads.COMMON["area_m2"]
+    for i in range(n):
+        nps = int(logu(u[4, i], *per_species))
+        out.append(dict(
+            workloads.COMMON, gap_m=gap, pressure_pa=logu(u[0, i], 1.0, 20.0),
+            v_rf_amp_v=100.0 + 400.0 * float(u[1, i]),
+            steps_per_rf=int(round(logu(u[2, i], 500, 4000))),
+            n_cells=int(round(logu(u[3, i], 100, 800))), weight=dens * area * gap / nps,
+            refl_e=0.7 * float(u[5, i]), gamma_see=0.4 * float(u[6, i]), init_per_species=nps,
+            capacity_per_species=8 * nps + 4096, instance=i, eepf_bins=N_EEPF,
+            eepf_emax_ev=EEPF_EMAX, precision=pic.PIC_FP32))
+    return out
+
+
+def features(c: dict) -> np.ndarray:
+    """The 7 inputs, scaled to about [-1, 1]: log p, V, log dt, log dx, log W, R, gamma."""
+    dt = 1.0 / (c["f_rf_hz"] * c["steps_per_rf"])
+    dx = c["gap_m"] / c["n_cells"]
+    return np.array([
+        (np.log(c["pressure_pa"]) - np.log(np.sqrt(20.0))) / np.log(np.sqrt(20.0)),
+        (c["v_rf_amp_v"] - 300.0) / 200.0,
+        (np.log(dt) - np.log(1.0 / (13.56e6 * np.sqrt(500 * 4000)))) / np.log(np.sqrt(8.0)),
+        (np.log(dx) - np.log(0.025 / np.sqrt(100 * 800))) / np.log(np.sqrt(8.0)),
+        (np.log(c["weight"]) - np.log(1e4)) / np.log(4.0),
+        c["refl_e"] / 0.35 - 1.0, c["gamma_see"] / 0.2 - 1.0], dtype=np.float32)
+
+
+def targets(diag: dict, gap: float) -> np.ndarray:
+    """192 outputs: log10 of the electron density (m^-3, floored) at 128 points of x/L, then
+    log10 of the centre EEPF (floored) in its 64 bins."""
+    ne = np.asarray(diag["n_e"], dtype=np.float64)
+    xs = np.linspace(0.0, 1.0, len(ne))
+    prof = np.interp(np.linspace(0.0, 1.0, N_PROFILE), xs, ne)
+    eepf = np.asarray(diag["eepf"], dtype=np.float64)
+    return np.concatenate([np.log10(prof + N_FLOOR),
+                           np.log10(np.maximum(eepf, 0.0) + F_FLOOR)]).astype(np.float32)
+
+
+def run_scan(settings: list[dict], warm_cycles: float = 1.0, avg_cycles: float = 1.0,
+             members: int = 128, stream=None):
+    """Run every setting with the FP32 ensemble: warm_cycles RF periods, then averages over
+    avg_cycles periods.  Returns (features [n, 7], targets [n, 192], PIC diagnostics list,
+    GPU seconds spent)."""
+    import torch
+
+    st = stream if stream is not None else torch.cuda.Stream()
+    X, Y, D = [], [], []
+    t0 = time.perf_counter()
+    for k in range(0, len(settings), members):
+        part = settings[k:k + members]
+        with torch.cuda.stream(st):
+            sims = [pic.Simulation(c) for c in part]
+            warm = [int(warm_cycles * c["steps_per_rf"]) for c in part]
+            ens = pic.Ensemble(sims, warm)
+            ens.step(max(warm))
+            _sync(ens)
+            for s in sims:
+                s.reset_averages()
+            ens.close()
+            full = [w + int(avg_cycles * c["steps_per_rf"]) for w, c in zip(warm, part)]
+            ens = pic.Ensemble(sims, full)
+            ens.step(max(f - w for f, w in zip(full, warm)))
+            _sync(ens)
+            ens.close()
+        for c, s in zip(part, sims):
+            d = s.diag()
+            X.append(features(c))
+            Y.append(targets(d, c["gap_m"]))
+            D.append({k2: d[k2] for k2 in ("omega_pe_dt", "dx_over_lambda_d", "p_coll_e",
+                                           "n_e_center", "te_center_ev", "return_code")})
+        del sims
+    torch.cuda.synchronize()
+    return np.array(X), np.array(Y), D, time.perf_counter() - t0
+
+
+def _sync(ens):
+    try:
+        ens.sync()
+    except pic.PicError as e:  # a setting that outgrew its capacity: counted, not fatal
+        if e.code != -3:
+            raise
+
+
+class Surrogate:
+    """The network with its output standardisation."""
+
+    def __init__(self, batch_max: int = 1024, seed: int = 1):
+        self.net = pic.Mlp(batch_max, seed)
+        self.mu = np.zeros(192, np.float32)
+        self.sd = np.ones(192, np.float32)
+
+    def fit(self, X: np.ndarray, Y: np.ndarray, epochs: int = 400, lr: float = 2e-3,
+            batch: int = 256, seed: int = 0) -> list[float]:
+        import torch
+
+        self.mu = Y.mean(axis=0).astype(np.float32)
+        self.sd = (Y.std(axis=0) + 1e-3).astype(np.float32)
+        Z = (Y - self.mu) / self.sd
+        n = (len(X) // batch) * batch
+        if n == 0:
+            raise ValueError("need at least one batch of training settings")
+        rng = np.random.default_rng(seed)
+        Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+        Zd = torch.from_numpy(np.ascontiguousarray(Z, np.float32)).cuda()
+        losses = []
+        for ep in range(epochs):
+            perm = torch.from_numpy(rng.permutation(len(X))[:n]).cuda()
+            for b in range(0, n, batch):
+                idx = perm[b:b + batch]
+                last = ep == epochs - 1 and b + batch >= n
+                loss = self.net.train_step(Xd[idx].contiguous(), Zd[idx].contiguous(), lr,
+                                           want_loss=(b == 0 or last))
+                if loss is not None:
+                    losses.append(loss)
+        return losses
+
+    def predict(self, X: np.ndarray) -> np.ndarray:
+        import torch
+
+        out = []
+        for b in range(0, len(X), self.net.batch_max):
+            xd = torch.from_numpy(np.ascontiguousarray(X[b:b + self.net.batch_max], np.float32))
+            out.append(self.net.forward(xd.cuda()).cpu().numpy())
+        return np.concatenate(out) * self.sd + self.mu
+
+
+def density(Y: np.ndarray) -> np.ndarray:
+    """Electron density profiles (m^-3) from outputs."""
+    return np.maximum(10.0 ** Y[:, :N_PROFILE] - N_FLOOR, 0.0)
+
+
+def profile_error(Y_pred: np.ndarray, Y_pic: np.ndarray) -> np.ndarray:
+    """Per setting: mean |n_pred - n_pic| over the profile / mean n_pic (the plain method's
+    profile is the judge)."""
+    a, b = density(Y_pred), density(Y_pic)
+    return np.abs(a - b).mean(axis=1) / np.maximum(b.mean(axis=1), 1.0)
+
+
+def accuracy_flags(X_settings: list[dict], Y: np.ndarray) -> np.ndarray:
+    """Settings likely to break the §3.5 accuracy criteria, from (predicted) outputs: the
+    plasma frequency and Debye length follow from the centre density and the centre EEPF's
+    mean energy; P_coll follows from the setting alone (electron collision probability)."""
+    flags = []
+    for c, y in zip(X_settings, Y):
+        n_c = float(density(y[None])[0][N_PROFILE // 2])
+        e = (np.arange(N_EEPF) + 0.5) * EEPF_EMAX / N_EEPF
+        f = np.maximum(10.0 ** y[N_PROFILE:] - F_FLOOR, 0.0)
+        w = f * np.sqrt(e)
+        mean_e = float((w * e).sum() / w.sum()) if w.sum() > 0 else 0.0
+        te = 2.0 / 3.0 * mean_e
+        dt = 1.0 / (c["f_rf_hz"] * c["steps_per_rf"])
+        dx = c["gap_m"] / c["n_cells"]
+        wpe_dt = np.sqrt(n_c * QE * QE / (EPS0 * ME)) * dt
+        lam = np.sqrt(EPS0 * te / (n_c * QE)) if n_c > 0 and te > 0 else np.inf
+        flags.append((wpe_dt > 0.2, dx / lam > 1.0))
+    return np.array(flags, dtype=bool)
+
+
+def pic_flags(D: list[dict]) -> np.ndarray:
+    return np.array([(d["omega_pe_dt"] > 0.2, d["dx_over_lambda_d"] > 1.0) for d in D], bool)
