@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--ensemble-members", type=int, default=64)
     ap.add_argument("--precisions", default="fp32,fp64",
                     help="comma list; the first is the headline, the others are reported beside it")
@@ -362,6 +363,56 @@ def measure_ensemble(args, torch, dist, rank: int) -> dict:
     return out
 
 
+def measure_surrogate(torch) -> dict:
+    """The surrogate: a 384-setting scan run by the FP32 ensemble (half an RF
+    period to warm up, half to average), the network trained on 320 settings by the
+    tensor-core kernels, judged on the 64 held-out settings by the plain method's profiles;
+    plus the tensor-core GEMM rate of its widest layer at batch 1024."""
+    from paper_2109_04469_gb300 import pic, surrogate as S
+
+    settings = S.sample_settings(384, seed=11)
+    X, Y, D, pic_s = S.run_scan(settings, warm_cycles=0.5, avg_cycles=0.5)
+    tr, te = np.arange(320), np.arange(320, 384)
+    sur = S.Surrogate(batch_max=512, seed=4)
+    t = time.perf_counter()
+    losses = sur.fit(X[tr], Y[tr], epochs=300)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t
+    t = time.perf_counter()
+    P = sur.predict(X[te])
+    net_s = time.perf_counter() - t
+    err = S.profile_error(P, Y[te])
+    base = S.profile_error(np.repeat(Y[tr].mean(axis=0, keepdims=True), len(te), 0), Y[te])
+    agree = (S.accuracy_flags([settings[i] for i in te], P) ==
+             S.pic_flags([D[i] for i in te])).mean(axis=0)
+    # tensor-core rate of the network's forward pass at batch 1024 (three GEMMs and their
+    # epilogues, enqueued back to back; events around 50 passes)
+    net = pic.Mlp(1024, seed=1)
+    xb = torch.randn(1024, 7, device="cuda")
+    net.forward(xb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(50):
+        net.forward(xb)
+    e1.record()
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 50
+    fwd_flop = 2.0 * 1024 * (16 * 256 + 256 * 256 + 256 * 192)
+    return {"settings": len(settings), "held_out": len(te),
+            "held_out_profile_error_mean": float(err.mean()),
+            "held_out_profile_error_median": float(np.median(err)),
+            "training_mean_error": float(base.mean()),
+            "flag_agreement": [float(v) for v in agree],
+            "scan_gpu_s_per_setting": pic_s / len(settings),
+            "network_s_per_setting": net_s / len(te), "fit_s": fit_s,
+            "final_loss": float(losses[-1]),
+            "forward_1024_us": fwd_ms * 1e3,
+            "forward_tflops": fwd_flop / (fwd_ms * 1e-3) / 1e12,
+            "note": "scan runs are 1 RF period from a uniform load (not converged "
+                    "discharges); the network is tiny, so its kernels are launch and latency "
+                    "bound, far from the tensor-core peak"}
+
+
 def reduce_ranks(torch, dist, step_ms: float, parts: int, device: str = "cuda"):
     """Whole-job figures of the replicas: the slowest rank's time, every rank's particles."""
     if not dist:
@@ -460,6 +511,8 @@ def main():
                            "births (counted), which is what a status of -3 reports"}
         if "fp64" in runs and "fp64" != head_prec:
             line["ensemble"]["speedup_vs_fp64_plain"] = ev / line["fp64_plain"]["value"]
+    if not args.no_surrogate and rank == 0:
+        line["surrogate"] = measure_surrogate(torch)
     if "e2e" in head:
         line["e2e"] = head["e2e"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
