@@ -322,7 +322,25 @@ __device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, Comp
   const int Gp = prefix_stride(G);
   const long long N2[2] = {K.st->n_snap[0], K.st->n_snap[1]};  // loads overlap the staging
   const unsigned nid2[2] = {K.st->id_snap[0], K.st->id_snap[1]};
-  if ((gstride & 3) == 0) {  // rows start on 16-byte boundaries: 16-byte loads, all in flight
+  if (gstride == G && (G & 3) == 0) {  // one contiguous block: 16-byte loads, all in flight
+    constexpr int kBatch = 12;
+    const int4* src = reinterpret_cast<const int4*>(K.hole_cnt[0]);
+    int4* dst = reinterpret_cast<int4*>(sp);
+    const int n4 = kA * G / 4;
+    for (int i0 = threadIdx.x; i0 < n4; i0 += kBatch * NT) {
+      int4 v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int i = i0 + u * NT;
+        if (i < n4) v[u] = __ldcg(src + i);
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int i = i0 + u * NT;
+        if (i < n4) dst[i] = v[u];
+      }
+    }
+  } else if ((gstride & 3) == 0) {  // rows on 16-byte boundaries: 16-byte loads, all in flight
     const int n4 = Gp / 4;
     for (int c0 = threadIdx.x; c0 < n4; c0 += 2 * NT) {
       int4 v[kA][2];
