@@ -327,7 +327,7 @@ __device__ __forceinline__ void put_rec(float* list, size_t cap, long long slot,
 }
 
 // A warp's staging of one 128-particle tile (bulk-copy destination; 16-byte aligned fields).
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 struct WarpTile {
   unsigned ccd[128];  // cell | countdown << 16
   float2 ov[128];     // off, vx
@@ -762,6 +762,81 @@ __device__ bool grid_barrier(EnsDev* E) {
   return sOk != 0;
 }
 
+// Phase 2 of an ensemble step (after the grid barrier), out of line so that its registers do
+// not add to the particle phase's.
+__device__ __noinline__ void ensemble_phase2(EnsDev* E, unsigned par, unsigned sEstep, int n,
+                                             const long long* sNe, const long long* sNi,
+                                             long long* sIt, const int* sG, unsigned char* esm,
+                                             CompactTot* sT) {
+  // phase 2
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) E->estep = sEstep + 1u;
+    for (int i = threadIdx.x; i < n * 5; i += blockDim.x) E->tot[par ^ 1u][i / 5][i % 5] = 0;
+    if (threadIdx.x == 0) E->next_chunk[par ^ 1u] = 0u;
+  }
+  // items of every simulation, from the totals
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    long long items = 0;
+    if (sG[s] > 0) {
+      const int* t = E->tot[par][s];
+      const long long cap = E->sims[s]->cap;
+      const long long N2[2] = {sNe[s], sNi[s]};
+      const long long H2[2] = {t[0], t[1]}, B2[2] = {(long long)t[2] + t[3], t[4]};
+      for (int sp = 0; sp < 2; ++sp) {
+        const long long limit = cap - (N2[sp] - H2[sp]);
+        const long long beff = B2[sp] < limit ? B2[sp] : limit;
+        const long long nn = N2[sp] - H2[sp] + beff;
+        items += beff + (H2[sp] > beff ? N2[sp] - nn : 0);
+      }
+    }
+    sIt[s] = items;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long run = 0;
+    for (int s = 0; s < n; ++s) {
+      const long long v = sIt[s];
+      sIt[s] = run;
+      run += v;
+    }
+    sIt[n] = run;
+  }
+  __syncthreads();
+  if ((int)blockIdx.x < n) {
+    const int s = blockIdx.x;
+    if (sG[s] > 0) {
+      const DevCtx& K = *E->sims[s];
+      if (threadIdx.x < 2) {
+        const int sp = threadIdx.x;
+        const int* t = E->tot[par][s];
+        CompactTot c;
+        c.N = sp ? sNi[s] : sNe[s];
+        c.H = t[sp];
+        c.B = sp ? t[4] : (long long)t[2] + t[3];
+        const long long limit = K.cap - (c.N - c.H);
+        c.Beff = c.B < limit ? c.B : limit;
+        c.Nn = c.N - c.H + c.Beff;
+        c.nid = K.st->id_snap[sp];
+        publish_counts(K, sp, c);
+      }
+      advance_field(K, esm);
+    }
+    return;
+  }
+  const int nb = gridDim.x - n, j = blockIdx.x - n;
+  const long long I = sIt[n];
+  const long long lo = I * j / nb, hi = I * (j + 1) / nb;
+  int* sp = reinterpret_cast<int*>(esm);
+  for (int s = 0; s < n && lo < hi; ++s) {
+    const long long a = max(lo, sIt[s]) - sIt[s], b = min(hi, sIt[s + 1]) - sIt[s];
+    if (a >= b) continue;
+    const DevCtx& K = *E->sims[s];
+    list_prefixes<kBlock>(K, sG[s], E->gstride[s], sp, sT);
+    place_items<Fp32Moves>(K, sG[s], sp, sT, a + threadIdx.x, b, (long long)blockDim.x);
+    __syncthreads();
+  }
+}
+
 // One step of every simulation of the ensemble that has not reached its target step.
 // Phase 1: the particle passes.  Each simulation's particles (both species) are cut into G_s
 // list owners of about E->unit particles, grouped in chunks of one owner per warp; blocks
@@ -899,73 +974,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
       for (int k = 0; k < kStages; ++k) mbar_inval(&P.bar[k]);
   }
   if (!grid_barrier(E)) return;
-  // phase 2
-  if (blockIdx.x == 0) {
-    if (threadIdx.x == 0) E->estep = sEstep + 1u;
-    for (int i = threadIdx.x; i < n * 5; i += blockDim.x) E->tot[par ^ 1u][i / 5][i % 5] = 0;
-    if (threadIdx.x == 0) E->next_chunk[par ^ 1u] = 0u;
-  }
-  // items of every simulation, from the totals
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    long long items = 0;
-    if (sG[s] > 0) {
-      const int* t = E->tot[par][s];
-      const long long cap = E->sims[s]->cap;
-      const long long N2[2] = {sNe[s], sNi[s]};
-      const long long H2[2] = {t[0], t[1]}, B2[2] = {(long long)t[2] + t[3], t[4]};
-      for (int sp = 0; sp < 2; ++sp) {
-        const long long limit = cap - (N2[sp] - H2[sp]);
-        const long long beff = B2[sp] < limit ? B2[sp] : limit;
-        const long long nn = N2[sp] - H2[sp] + beff;
-        items += beff + (H2[sp] > beff ? N2[sp] - nn : 0);
-      }
-    }
-    sIt[s] = items;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long run = 0;
-    for (int s = 0; s < n; ++s) {
-      const long long v = sIt[s];
-      sIt[s] = run;
-      run += v;
-    }
-    sIt[n] = run;
-  }
-  __syncthreads();
-  if ((int)blockIdx.x < n) {
-    const int s = blockIdx.x;
-    if (sG[s] > 0) {
-      const DevCtx& K = *E->sims[s];
-      if (threadIdx.x < 2) {
-        const int sp = threadIdx.x;
-        const int* t = E->tot[par][s];
-        CompactTot c;
-        c.N = sp ? sNi[s] : sNe[s];
-        c.H = t[sp];
-        c.B = sp ? t[4] : (long long)t[2] + t[3];
-        const long long limit = K.cap - (c.N - c.H);
-        c.Beff = c.B < limit ? c.B : limit;
-        c.Nn = c.N - c.H + c.Beff;
-        c.nid = K.st->id_snap[sp];
-        publish_counts(K, sp, c);
-      }
-      advance_field(K, esm);
-    }
-    return;
-  }
-  const int nb = gridDim.x - n, j = blockIdx.x - n;
-  const long long I = sIt[n];
-  const long long lo = I * j / nb, hi = I * (j + 1) / nb;
-  int* sp = reinterpret_cast<int*>(esm);
-  for (int s = 0; s < n && lo < hi; ++s) {
-    const long long a = max(lo, sIt[s]) - sIt[s], b = min(hi, sIt[s + 1]) - sIt[s];
-    if (a >= b) continue;
-    const DevCtx& K = *E->sims[s];
-    list_prefixes<kBlock>(K, sG[s], E->gstride[s], sp, sT);
-    place_items<Fp32Moves>(K, sG[s], sp, sT, a + threadIdx.x, b, (long long)blockDim.x);
-    __syncthreads();
-  }
+  ensemble_phase2(E, par, sEstep, n, sNe, sNi, sIt, sG, esm, sT);
 }
 
 // ------------------------------------------------------------------------ launchers
