@@ -233,7 +233,9 @@ int pic_ensemble_workspace_bytes(int n, size_t* bytes);
  * workspaces likewise).  target_steps[i] >= 0: the step index at which member i stops.
  * Records the step launch as a CUDA graph (falls back to direct launches if recording
  * fails).  Synchronises the stream.  PIC_ERR_PARAM for a member that is not PIC_FP32, on
- * another stream or repeated; PIC_ERR_WORKSPACE for a missing or small workspace. */
+ * another stream, repeated, or too large for the launch's shared memory (more than about
+ * 4000 x 3800 / 2 superparticles of capacity per species); PIC_ERR_WORKSPACE for a missing
+ * or small workspace. */
 int pic_ensemble_create(pic_handle* const* sims, int n, const int64_t* target_steps,
                         void* workspace, size_t workspace_bytes, pic_ensemble** out);
 

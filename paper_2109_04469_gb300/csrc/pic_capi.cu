@@ -1072,6 +1072,9 @@ int pic_ensemble_create(pic_handle* const* sims, int n, const int64_t* target_st
     h->target[i] = target_steps[i];
     h->gcap[i] = (int)std::min<long long>(nl - 4, gcap_lim);
     h->gstride[i] = (int)nl;
+    // with at most gcap owners, an owner must still fit the shared counters' bound
+    if ((2 * sims[i]->p.capacity_per_species + h->gcap[i] - 1) / h->gcap[i] + 64 > kMaxEnsUnit)
+      return fail(PIC_ERR_PARAM);
   }
   // phase-1 order: members whose electrons are collision candidates most often (the costly
   // particles) first, so the last chunks taken are cheap ones

@@ -853,6 +853,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
   __shared__ long long sNe[kMaxEnsemble], sNi[kMaxEnsemble], sIt[kMaxEnsemble + 1];
   __shared__ unsigned sStep[kMaxEnsemble];
   __shared__ int sG[kMaxEnsemble], sC0[kMaxEnsemble + 1], sOrd[kMaxEnsemble];
+  __shared__ int sUpw[kMaxEnsemble];  // owners per warp per chunk
   __shared__ unsigned sChunk;
   __shared__ unsigned long long sCnt[kNumCounters];
   __shared__ CompactTot sT[2];
@@ -870,6 +871,11 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
     sNi[s] = ni;
     sStep[s] = step;
     sG[s] = active ? (int)g : 0;
+    // owners per warp between counter flushes: every owner holds at most
+    // ceil(N / G) + 64 particles (32-particle rounding per species); keep the warp's sum
+    // within kMaxEnsUnit so the 32-bit shared counters stay in range
+    const long long per = (ne + ni + g - 1) / g + 64;
+    sUpw[s] = (int)max(1ll, (long long)kMaxEnsUnit / per);
     if (active && blockIdx.x == 0) snapshot_pass(*E->sims[s], step, ne, ni);
   }
   if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
@@ -881,7 +887,8 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
       const int s = E->order[k];
       sOrd[k] = s;
       sC0[k] = run;
-      run += (sG[s] + kWarps32 - 1) / kWarps32;
+      const int span = kWarps32 * sUpw[s];
+      run += (sG[s] + span - 1) / span;
     }
     sC0[n] = run;
   }
@@ -939,7 +946,9 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
       const long long ne = sNe[s], ni = sNi[s];
       const int G = sG[s], gs = E->gstride[s];
       unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
-      const long long g = (long long)(c - (unsigned)sC0[k]) * kWarps32 + warp;
+      const int upw = sUpw[s];
+      for (int u = 0; u < upw; ++u) {
+      const long long g = (long long)(c - (unsigned)sC0[k]) * kWarps32 * upw + u * kWarps32 + warp;
       if (g < G) {
         // after a timed-out wait (status set) the warp's remaining owners list nothing
         const long long q0 = range_begin(ne, (int)g, G), q1 = range_begin(ne, (int)g + 1, G);
@@ -965,7 +974,8 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
           if (bi) atomicAdd(&t[4], bi);
         }
       }
-      flush32(K, sC, Cn);  // one owner per warp per chunk: the counters stay in range
+      }
+      flush32(K, sC, Cn);  // upw owners per warp per chunk: the counters stay in range
     }
     if (cur >= 0 && threadIdx.x < kNumCounters && sCnt[threadIdx.x])
       atomicAdd(&E->sims[sOrd[cur]]->counters[threadIdx.x], sCnt[threadIdx.x]);
