@@ -263,6 +263,14 @@ int pic_ensemble_info(pic_ensemble* e, int32_t* out);
 /* Release the ensemble (host memory and its graph; members and workspaces stay). */
 void pic_ensemble_free(pic_ensemble* e);
 
+/* Failure detection without a fault: runs one bulk-copy barrier wait that no copy will
+ * complete (about 0.1 s of polls) and one grid barrier that expects one block more than
+ * launched (about 0.5 s), in the caller's DEVICE workspace of at least
+ * pic_ensemble_workspace_bytes(1) + 256 bytes.  codes[0], codes[1] receive the status each
+ * wait reported: PIC_ERR_TIMEOUT when the bound works.  Synchronises. */
+int pic_selftest_waits(void* workspace, size_t workspace_bytes, void* cuda_stream,
+                       int32_t* codes);
+
 /* ---------------------------------------------------------------------------------------
  * Surrogate network (the paper has none): BF16 tensor-core kernels.
  * --------------------------------------------------------------------------------------- */

@@ -1184,6 +1184,27 @@ int pic_ensemble_info(pic_ensemble* e, int32_t* out) {
   return PIC_OK;
 }
 
+int pic_selftest_waits(void* workspace, size_t workspace_bytes, void* cuda_stream,
+                       int32_t* codes) {
+  size_t need = 0;
+  pic_ensemble_workspace_bytes(1, &need);
+  need += 256;
+  if (!codes || !workspace || workspace_bytes < need ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return PIC_ERR_PARAM;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  EnsDev* E = static_cast<EnsDev*>(workspace);
+  int* st = reinterpret_cast<int*>(static_cast<char*>(workspace) + need - 256);
+  int h[2] = {0, 0};
+  PIC_CUDA(cudaMemsetAsync(workspace, 0, need, s));
+  PIC_CUDA(launch_selftest_waits(E, st, s));
+  PIC_CUDA(cudaMemcpyAsync(h, st, sizeof h, cudaMemcpyDeviceToHost, s));
+  PIC_CUDA(cudaStreamSynchronize(s));
+  codes[0] = status_code(h[0]);
+  codes[1] = status_code(h[1]);
+  return PIC_OK;
+}
+
 void pic_ensemble_free(pic_ensemble* e) {
   if (!e) return;
   drop_graph(e);

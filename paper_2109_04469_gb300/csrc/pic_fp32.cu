@@ -732,7 +732,7 @@ __global__ void k_deposit32(DevCtx K, int s, int buf, long long n) {
 // meet at a grid barrier; the wait is bounded and reports kStTimeout instead of hanging.
 constexpr long long kGridSpinLimit = 1ll << 22;  // polls, ~128 ns apart (~0.5 s)
 
-__device__ bool grid_barrier(EnsDev* E) {
+__device__ bool grid_barrier(EnsDev* E, unsigned expected = 0u) {
   __shared__ int sOk;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -740,7 +740,8 @@ __device__ bool grid_barrier(EnsDev* E) {
     const unsigned g0 = *gen;
     __threadfence();
     int ok = 1;
-    if (atomicAdd(&E->bar_count, 1u) == gridDim.x - 1) {
+    const unsigned arrivals = expected ? expected : gridDim.x;
+    if (atomicAdd(&E->bar_count, 1u) == arrivals - 1) {
       E->bar_count = 0u;
       __threadfence();
       atomicAdd(&E->bar_gen, 1u);
@@ -985,6 +986,26 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
   }
   if (!grid_barrier(E)) return;
   ensemble_phase2(E, par, sEstep, n, sNe, sNi, sIt, sG, esm, sT);
+}
+
+// Self-test of the bounded waits (failure detection without a fault): a bulk-copy barrier
+// that is told to expect bytes no copy will deliver, and a grid barrier that is told to expect
+// one block more than the launch has.  Both must give up and record kStTimeout.
+__global__ void k_selftest_waits(EnsDev* E, int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1u);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, 16u);  // 16 bytes announced, none will arrive
+    if (!mbar_wait(&bar, 0u, 200)) atomicOr(&status[0], kStTimeout);  // ~0.1 s of polls
+  }
+  __syncthreads();
+  if (!grid_barrier(E, gridDim.x + 1u)) atomicOr(&status[1], kStTimeout);
+}
+
+cudaError_t launch_selftest_waits(EnsDev* E, int* status, cudaStream_t s) {
+  k_selftest_waits<<<1, 32, 0, s>>>(E, status);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------ launchers

@@ -42,6 +42,8 @@ size_t ensemble_smem_bytes(int nx_max, int gcap_max);
 cudaError_t configure_ensemble(size_t smem);
 int ensemble_blocks_per_sm(size_t smem);
 cudaError_t launch_ensemble(EnsDev* E, int grid, size_t smem, cudaStream_t s);
+// bounded-wait self-test: status[0] bulk-copy barrier, status[1] grid barrier (kStTimeout)
+cudaError_t launch_selftest_waits(EnsDev* E, int* status, cudaStream_t s);
 int push_fp32_blocks_per_sm(int nx);
 
 }  // namespace pic

@@ -66,9 +66,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   return ok != 0u;
 }
 
-// Bounded wait for phase `parity` of `bar`; false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (long long it = 0; it < kSpinLimit; ++it)
+// Bounded wait for phase `parity` of `bar`; false if `limit` polls were not enough.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          long long limit = kSpinLimit) {
+  for (long long it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -123,6 +123,7 @@ def lib() -> C.CDLL:
                 "pic_ensemble_autotune": (C.c_int, [P, C.c_int32, P]),
                 "pic_ensemble_info": (C.c_int, [P, P]),
                 "pic_ensemble_free": (None, [P]),
+                "pic_selftest_waits": (C.c_int, [P, C.c_size_t, P, P]),
                 "pic_field_solve_static": (C.c_int, [P, P, C.c_int32, C.c_double, C.c_double,
                                                      C.c_double, C.c_double, P, P, P]),
             }
@@ -498,4 +499,19 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def selftest_waits(stream=None) -> tuple[int, int]:
+    """Run the bounded-wait self-test; returns the codes of the bulk-copy barrier and the grid
+    barrier waits (PIC_ERR_TIMEOUT, -6, when each gave up as designed)."""
+    import torch
+
+    nb = C.c_size_t(0)
+    _check(lib().pic_ensemble_workspace_bytes(1, C.byref(nb)), "pic_ensemble_workspace_bytes")
+    ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    codes = np.zeros(2, dtype=np.int32)
+    _check(lib().pic_selftest_waits(C.c_void_p(ws.data_ptr()), nb.value + 256,
+                                    C.c_void_p(s.cuda_stream), _ptr(codes)), "pic_selftest_waits")
+    return int(codes[0]), int(codes[1])
 

@@ -167,3 +167,13 @@ def test_handles_of_different_grids_coexist():
             sim.step(3)
             assert sim.sync() == 0
 
+
+
+def test_bounded_waits_report_timeouts():
+    """Failure detection without a fault: a bulk-copy barrier nothing completes and a grid
+    barrier expecting a block that does not exist both give up and report PIC_ERR_TIMEOUT,
+    and the context stays usable afterwards."""
+    assert pic.selftest_waits() == (-6, -6)
+    sim = pic.Simulation(_cfg(0))
+    sim.step(3)
+    assert sim.sync() == 0

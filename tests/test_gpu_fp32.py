@@ -138,3 +138,17 @@ def test_fp32_full_size_workload_runs():
     assert int(g["Ce"].sum()) == ne * 2**32 and int(g["Ci"].sum()) == ni * 2**32
     assert 1.9e6 < ne < 2.1e6 and 1.9e6 < ni < 2.1e6
     sim.close()
+
+
+def test_fp32_largest_grid_runs():
+    """The largest grid the handles accept (4096 cells): shared-memory tables of 4097 nodes."""
+    cfg = _cfg(n_cells=4096, init_per_species=20000, capacity_per_species=65536)
+    sim = pic.Simulation(cfg)
+    sim.step(10)
+    assert sim.sync() == 0
+    g = sim.grid()
+    ne, ni = sim.counts()
+    assert int(g["Ce"].sum()) == ne * 2**32 and int(g["Ci"].sum()) == ni * 2**32
+    with pytest.raises(pic.PicError):
+        pic.Simulation(_cfg(n_cells=4097))
+

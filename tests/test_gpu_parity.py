@@ -83,7 +83,7 @@ def test_field_bit_exact():
     sim.close()
 
 
-@pytest.mark.parametrize("nc", [2, 3, 401, 1024])
+@pytest.mark.parametrize("nc", [2, 3, 401, 1024, 4096])
 def test_deposit_and_field_random_positions(nc):
     cfg = workloads.params("ccp_5pa_150v_128c", n_cells=nc, init_per_species=0,
                            capacity_per_species=50_000)
