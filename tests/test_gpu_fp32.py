@@ -6,7 +6,9 @@ The FP32 path is not bit-identical to the oracle; its bar is:
   * with a negligible self-field (no chaos) trajectories follow the FP64 oracle to FP32
     rounding, with the same surface decisions;
   * RF-averaged densities, the centre EEPF mean energy and the ion flux agree with the
-    oracle within 3 combined standard errors over independent seeds.
+    oracle within 3 combined standard errors over independent seeds, and so do the density
+    profile (8 segments) and the EEPF (5 energy bands), bin by bin (|z| < 4, sum of z^2
+    below the 99.9 % point of chi^2(13)).
 """
 import math
 
@@ -102,8 +104,18 @@ def _averages(run, cfg, steps, avg_from):
     L = cfg["gap_m"]
     x = np.linspace(0, L, cfg["n_cells"] + 1)
     trap = lambda y: float(np.sum((y[1:] + y[:-1]) * 0.5 * np.diff(x)))
-    return dict(ne=trap(d["n_e"]) / L, ni=trap(d["n_i"]) / L, flux=d["ion_flux"],
-                te=d["te_center_ev"])
+    out = dict(ne=trap(d["n_e"]) / L, ni=trap(d["n_i"]) / L, flux=d["ion_flux"],
+               te=d["te_center_ev"])
+    # the profile in 8 equal segments of the gap (mean density of each)
+    nodes = np.array_split(np.arange(cfg["n_cells"] + 1), 8)
+    for k, idx in enumerate(nodes):
+        out[f"ne{k}"] = float(np.mean(d["n_e"][idx]))
+    # the EEPF as probability mass in 5 energy bands: sum of f sqrt(eps) d(eps)
+    e = np.asarray(d["eepf_energy"])
+    mass = np.asarray(d["eepf"]) * np.sqrt(e) * (cfg["eepf_emax_ev"] / len(e))
+    for k, (lo, hi) in enumerate(((0, 2), (2, 5), (5, 10), (10, 20), (20, 50))):
+        out[f"f{k}"] = float(mass[(e >= lo) & (e < hi)].sum())
+    return out
 
 
 def test_fp32_statistics_match_oracle():
@@ -124,6 +136,19 @@ def test_fp32_statistics_match_oracle():
         se = math.sqrt(a.var(ddof=1) / seeds + b.var(ddof=1) / seeds)
         print(k, a.mean(), b.mean(), se)
         assert abs(a.mean() - b.mean()) <= 3 * se + 1e-12 * abs(b.mean()), (k, a.mean(), b.mean(), se)
+    # the density profile (8 segments) and the EEPF (5 bands): every bin within 4 combined
+    # standard errors, and the sum of squared z-scores below the 99.9 % point of chi^2(13)
+    zs = []
+    for k in [f"ne{i}" for i in range(8)] + [f"f{i}" for i in range(5)]:
+        a = np.array([r[k] for r in res["gpu"]])
+        b = np.array([r[k] for r in res["ref"]])
+        se = math.sqrt(a.var(ddof=1) / seeds + b.var(ddof=1) / seeds)
+        z = (a.mean() - b.mean()) / se if se > 0 else 0.0
+        print(k, a.mean(), b.mean(), "z", z)
+        zs.append(z)
+    zs = np.array(zs)
+    assert np.all(np.abs(zs) < 4.0), zs
+    assert float(np.sum(zs ** 2)) < 34.5, zs
 
 
 def test_fp32_full_size_workload_runs():
