@@ -277,8 +277,10 @@ int pic_selftest_waits(void* workspace, size_t workspace_bytes, void* cuda_strea
 
 /* C[m x n] = A[m x k] * B[n x k]^T on the tcgen05 tensor cores: A, B DEVICE arrays of BF16
  * (raw 16-bit patterns), row-major with k contiguous; C a DEVICE FP32 array, row-major.
- * FP32 accumulation.  m % 128 == 0, n % 16 == 0 with 16 <= n <= 256, k % 16 == 0, k >= 16
- * (PIC_ERR_PARAM otherwise).  Synchronises; PIC_ERR_TIMEOUT if the MMAs never completed. */
+ * FP32 accumulation.  m % 128 == 0, n % 16 == 0 with 16 <= n <= 4096, k % 16 == 0, k >= 16,
+ * a and b 16-byte aligned (PIC_ERR_PARAM otherwise).  Operands are read by TMA tensor copies
+ * into a 4-stage shared-memory ring; one CTA per 128 rows x (up to 256) columns.
+ * Synchronises; PIC_ERR_TIMEOUT if a pipeline wait or the MMAs never completed. */
 int pic_tc_gemm_bf16(const uint16_t* a, const uint16_t* b, float* c, int32_t m, int32_t n,
                      int32_t k, void* cuda_stream);
 

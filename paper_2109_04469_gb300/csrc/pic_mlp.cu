@@ -1,10 +1,14 @@
 // pic_mlp.cu -- the surrogate network of the parameter scans: a
 // 7 -> 256 -> 256 -> 192 MLP with GELU, BF16 weights and activations, FP32 accumulation,
 // trained and evaluated by this file's kernels.  Every matrix product runs on the tcgen05
-// tensor cores (pic_tc.cuh): operand tiles staged in shared memory in the canonical K-major
-// layout, the accumulator in tensor memory, read back for an FP32 epilogue.
+// tensor cores (pic_tc.cuh): operand tiles brought into shared memory by TMA tensor copies in
+// the canonical K-major layout through a multi-stage mbarrier ring, the accumulator in tensor
+// memory, read back for an FP32 epilogue.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include <cmath>
 #include <cstdint>
@@ -19,97 +23,10 @@ namespace pic {
 namespace {
 
 constexpr int kTcM = 128;        // rows of A per CTA (one MMA tile)
-constexpr int kKc = 64;          // K staged per shared-memory round (four MMA K-steps)
+constexpr int kKc = 64;          // K per pipeline stage (four MMA K-steps of 16)
+constexpr int kGemmStages = 4;   // stages of the TMA -> MMA ring
 constexpr int kGemmThreads = 128;
-
-size_t gemm_smem_bytes(int N) { return (size_t)kTcM * kKc * 2 + (size_t)N * kKc * 2; }
-
-// C[M x N] (FP32, row stride ldc) = A[M x K] * B[N x K]^T, A and B BF16 row-major (K
-// contiguous).  M % 128 == 0, N % 16 == 0 with 16 <= N <= 256, K % 16 == 0, K >= 16.
-// One CTA per 128 rows; thread 0 issues the MMAs; the four warps read back their 32 rows.
-__global__ void __launch_bounds__(kGemmThreads, 1)
-    k_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
-                float* __restrict__ C, int N, int K, int ldc, int* err) {
-  extern __shared__ __align__(1024) unsigned char tsm[];
-  unsigned char* sA = tsm;
-  unsigned char* sB = tsm + (size_t)kTcM * kKc * 2;
-  __shared__ __align__(8) unsigned long long bar;
-  __shared__ unsigned tslot;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kTcM;
-  const unsigned ncols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
-  if (warp == 0) tc_alloc(&tslot, ncols);
-  if (tid == 0) {
-    mbar_init(&bar, 1u);
-    fence_mbar_init();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const unsigned taddr = tslot;
-  const unsigned idesc = tc_idesc_bf16(kTcM, N);
-  unsigned phase = 0;
-  for (int k0 = 0; k0 < K; k0 += kKc) {
-    const int kc = min(kKc, K - k0);  // a multiple of 16
-    const int pieces = kc / 8;        // 16-byte pieces of a row
-    const unsigned sbo = (unsigned)pieces * kTcLbo;
-    for (int i = tid; i < kTcM * pieces; i += kGemmThreads) {
-      const int r = i / pieces, kb = i - r * pieces;
-      const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + r) * K + k0 + 8 * kb);
-      *reinterpret_cast<uint4*>(sA + (r >> 3) * sbo + kb * kTcLbo + (r & 7) * 16) = v;
-    }
-    for (int i = tid; i < N * pieces; i += kGemmThreads) {
-      const int r = i / pieces, kb = i - r * pieces;
-      const uint4 v = *reinterpret_cast<const uint4*>(B + (size_t)r * K + k0 + 8 * kb);
-      *reinterpret_cast<uint4*>(sB + (r >> 3) * sbo + kb * kTcLbo + (r & 7) * 16) = v;
-    }
-    fence_proxy_async_smem();  // the tiles just written are read by the tensor core
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      for (int s = 0; s < kc / 16; ++s)  // K-step s covers core matrices 2s, 2s+1 along K
-        tc_mma_bf16(taddr, tc_smem_desc(sA + s * 2 * kTcLbo, kTcLbo, sbo),
-                    tc_smem_desc(sB + s * 2 * kTcLbo, kTcLbo, sbo), idesc, k0 > 0 || s > 0);
-      tc_commit(&bar);
-    }
-    // the MMAs read the tiles: wait before the next round overwrites them
-    if (!mbar_wait(&bar, phase)) {
-      if (lane == 0) atomicOr(err, 1);
-    }
-    phase ^= 1u;
-    tc_fence_after();
-  }
-  const int row = m0 + warp * 32 + lane;
-  for (int c = 0; c < N; c += 16) {
-    float v[16];
-    tc_ld16(taddr + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) C[(size_t)row * ldc + c + j] = v[j];
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tc_dealloc(taddr, ncols);
-}
-
-bool gemm_shape_ok(int M, int N, int K) {
-  return M > 0 && M % kTcM == 0 && N >= 16 && N <= 256 && N % 16 == 0 && K >= 16 &&
-         K % 16 == 0;
-}
-
-cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N,
-                        int K, int ldc, int* err, cudaStream_t s) {
-  // room for the widest B tile whatever N is, so no staging can reach past the allocation
-  static const cudaError_t configured = cudaFuncSetAttribute(
-      k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes(256));
-  if (configured != cudaSuccess) return configured;
-  (void)N;
-  k_gemm_bf16<<<M / kTcM, kGemmThreads, gemm_smem_bytes(256), s>>>(A, B, C, N, K, ldc, err);
-  return cudaGetLastError();
-}
-
-// ----------------------------------------------------------------- the network's kernels
-constexpr int kIn = 7, kInP = 16, kHid = 256, kOut = 192;
-constexpr int kNParams = kHid * kIn + kHid + kHid * kHid + kHid + kOut * kHid + kOut;
+constexpr int kGemmMaxBn = 256;
 
 // GELU, tanh form: g(z) = z/2 (1 + tanh(c (z + 0.044715 z^3))), c = sqrt(2/pi)
 __device__ __forceinline__ float gelu(float z) {
@@ -122,6 +39,255 @@ __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * z * z);
 }
 
+// What the GEMM does with its FP32 accumulator a = (A B^T)[row, col] (row-major arrays use the
+// GEMM's row stride ldc; transposed arrays Ht use ldt):
+//   kEpiStore     C[row, col] = a
+//   kEpiBias      C[row, col] = a + bias[col], rows < `rows` only (the linear output layer)
+//   kEpiBiasGelu  z = a + bias[col]; Z[row, col] = z; H[row, col] = Ht[col, row] = BF16(GELU(z))
+//   kEpiGeluGrad  g = a GELU'(Zin[row, col]); C[row, col] = g; H[row, col] (if H) and
+//                 Ht[col, row] = BF16(g)
+enum { kEpiStore = 0, kEpiBias = 1, kEpiBiasGelu = 2, kEpiGeluGrad = 3 };
+struct GemmEpi {
+  int mode = kEpiStore;
+  int rows = 0;
+  int ldt = 0;
+  const float* bias = nullptr;
+  const float* Zin = nullptr;
+  float* Z = nullptr;
+  __nv_bfloat16* H = nullptr;
+  __nv_bfloat16* Ht = nullptr;
+};
+
+// Shared memory of one CTA with B tiles of bn rows: kGemmStages x (A tile + B tile), each tile
+// K-major without swizzle as the TMA boxes write it, plus alignment slack.
+size_t gemm_smem_bytes(int bn) {
+  return (size_t)kGemmStages * (size_t)(kTcM + bn) * kKc * 2 + 1024;
+}
+
+// C[M x N] (FP32, row stride ldc) = A[M x K] * B[N x K]^T, A and B BF16 row-major (K
+// contiguous), read through the tensor maps ta (box 8 x 128) and tb (box 8 x bn).
+// CTA (x, y) owns rows [128 x, 128 x + 128) and columns [bn y, bn y + bn).
+//
+// Each stage holds K = 64 of both operands as eight TMA boxes of 8 elements (16 bytes) per
+// row: box kb lands at kb x rows x 16 bytes, row r at r x 16, so the 8-row x 16-byte core
+// matrices are contiguous, row groups 128 bytes apart (SBO) and K-neighbours rows x 16 bytes
+// apart (LBO).  Thread 0 fills the stages, thread 32 issues the MMAs and frees each stage by a
+// commit to its `empty` barrier; after the last K-step a commit to `done` releases the four
+// warps, which read their 32 accumulator lanes back from tensor memory.
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                float* __restrict__ C, int N, int K, int ldc, int bn, int vec4, GemmEpi E,
+                int* err) {
+  extern __shared__ __align__(1024) unsigned char gsm_raw[];
+  unsigned char* gsm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+  const unsigned stA = (unsigned)kTcM * kKc * 2, stB = (unsigned)bn * kKc * 2;
+  __shared__ __align__(8) unsigned long long full[kGemmStages], empty[kGemmStages], done;
+  __shared__ unsigned tslot;
+  __shared__ int issued, consumed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * bn;
+  const unsigned ncols = bn <= 32 ? 32u : (bn <= 64 ? 64u : (bn <= 128 ? 128u : 256u));
+  const int nk = (K + kKc - 1) / kKc;
+  if (warp == 0) tc_alloc(&tslot, ncols);
+  if (tid == 0) {
+    for (int s = 0; s < kGemmStages; ++s) {
+      mbar_init(&full[s], 1u);
+      mbar_init(&empty[s], 1u);
+    }
+    mbar_init(&done, 1u);
+    fence_mbar_init();
+    issued = 0;
+    consumed = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned taddr = tslot;
+  if (tid == 0) {  // producer
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % kGemmStages;
+      if (kc >= kGemmStages && !mbar_wait(&empty[s], (unsigned)(kc / kGemmStages - 1) & 1u)) {
+        atomicOr(err, 1);
+        break;
+      }
+      const int k0 = kc * kKc, nkb = min(8, (K - k0) / 8);
+      unsigned char* a = gsm + (size_t)s * (stA + stB);
+      unsigned char* b = a + stA;
+      mbar_arrive_expect_tx(&full[s], (unsigned)nkb * 16u * (unsigned)(kTcM + bn));
+      for (int kb = 0; kb < nkb; ++kb) {
+        tma_load_2d(a + kb * kTcM * 16, &ta, k0 + 8 * kb, m0, &full[s]);
+        tma_load_2d(b + kb * bn * 16, &tb, k0 + 8 * kb, n0, &full[s]);
+      }
+      issued = kc + 1;
+    }
+  } else if (tid == 32) {  // MMA issuer
+    const unsigned idesc = tc_idesc_bf16(kTcM, bn);
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % kGemmStages;
+      if (!mbar_wait(&full[s], (unsigned)(kc / kGemmStages) & 1u)) {
+        atomicOr(err, 1);
+        break;
+      }
+      tc_fence_after();
+      const int nks = min(8, (K - kc * kKc) / 8) / 2;
+      const unsigned char* a = gsm + (size_t)s * (stA + stB);
+      const unsigned char* b = a + stA;
+      for (int ks = 0; ks < nks; ++ks)
+        tc_mma_bf16(taddr, tc_smem_desc(a + ks * 2 * kTcM * 16, kTcM * 16, 128),
+                    tc_smem_desc(b + ks * 2 * bn * 16, bn * 16, 128), idesc, kc > 0 || ks > 0);
+      tc_commit(&empty[s]);
+      consumed = kc + 1;
+    }
+    tc_commit(&done);
+  }
+  __syncwarp();
+  if (!mbar_wait(&done, 0u)) {
+    if (lane == 0) atomicOr(err, 1);
+  }
+  tc_fence_after();
+  const int row = m0 + warp * 32 + lane;
+  for (int c = 0; c < bn && n0 + c < N; c += 16) {
+    float v[16];
+    tc_ld16(taddr + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
+    const size_t rb = (size_t)row * ldc + n0 + c;
+    const int col = n0 + c;
+    if (E.mode == kEpiStore) {
+      if (vec4) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(C + rb + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) C[rb + j] = v[j];
+      }
+    } else if (E.mode == kEpiBias) {
+      if (row < E.rows)
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(C + rb + j) =
+              make_float4(v[j] + E.bias[col + j], v[j + 1] + E.bias[col + j + 1],
+                          v[j + 2] + E.bias[col + j + 2], v[j + 3] + E.bias[col + j + 3]);
+    } else {
+      // row-major outputs as 16-byte stores of this thread's 16 columns; the transposed copy
+      // column by column (lanes hold consecutive rows, so each store is coalesced)
+      float o[16];
+      __align__(16) __nv_bfloat16 h[16];
+      if (E.mode == kEpiBiasGelu) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          o[j] = v[j] + E.bias[col + j];
+          h[j] = __float2bfloat16_rn(gelu(o[j]));
+        }
+      } else {
+        float z[16];
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(z + j) = *reinterpret_cast<const float4*>(E.Zin + rb + j);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          o[j] = v[j] * gelu_grad(z[j]);
+          h[j] = __float2bfloat16_rn(o[j]);
+        }
+      }
+      float* fo = E.mode == kEpiBiasGelu ? E.Z : C;
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(fo + rb + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
+      if (E.H) {
+        uint4* hd = reinterpret_cast<uint4*>(E.H + rb);
+        hd[0] = *reinterpret_cast<const uint4*>(h);
+        hd[1] = *reinterpret_cast<const uint4*>(h + 8);
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) E.Ht[(size_t)(col + j) * E.ldt + row] = h[j];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0)  // copies issued but never consumed (a timed-out MMA wait) land before exit
+    for (int kc = consumed; kc < issued; ++kc)
+      (void)mbar_wait(&full[kc % kGemmStages], (unsigned)(kc / kGemmStages) & 1u);
+  __syncthreads();
+  if (warp == 0) tc_dealloc(taddr, ncols);
+}
+
+bool gemm_shape_ok(int M, int N, int K) {
+  return M > 0 && M % kTcM == 0 && N >= 16 && N <= 4096 && N % 16 == 0 && K >= 16 &&
+         K % 16 == 0;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no libcuda link).
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of a row-major BF16 matrix [rows x K] (K contiguous) read in boxes of 8 x box_rows.
+bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int box_rows) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Width of the column tiles: the whole of N (up to 256) unless halving it still leaves
+// columns of at least 32 and the grid has fewer than 64 CTAs.
+int gemm_bn(int M, int N) {
+  auto up16 = [](int v) { return (v + 15) & ~15; };
+  int bn = std::min(up16(N), kGemmMaxBn);
+  while (bn > 32 && (M / kTcM) * ((N + bn - 1) / bn) < 64) bn = up16(bn / 2);
+  return bn;
+}
+
+// cudaErrorInvalidValue when an operand is not 16-byte aligned (the tensor maps need it)
+cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N,
+                        int K, int ldc, int* err, cudaStream_t s, const GemmEpi& epi = GemmEpi()) {
+  // room for the widest B tile whatever the launch, so no stage can reach past the allocation
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)gemm_smem_bytes(kGemmMaxBn));
+  if (configured != cudaSuccess) return configured;
+  const int bn = gemm_bn(M, N);
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, M, K, kTcM) || !make_map(&tb, B, N, K, bn)) return cudaErrorInvalidValue;
+  const int vec4 = (ldc % 4 == 0 && (reinterpret_cast<uintptr_t>(C) & 15u) == 0) ? 1 : 0;
+  // the fused epilogues store 16-byte vectors: row strides of 4 floats, aligned arrays
+  if (epi.mode != kEpiStore) {
+    const uintptr_t al = reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(epi.Z) |
+                         reinterpret_cast<uintptr_t>(epi.Zin) | reinterpret_cast<uintptr_t>(epi.H);
+    if (ldc % 8 != 0 || (al & 15u) != 0) return cudaErrorInvalidValue;
+  }
+  const dim3 grid((unsigned)(M / kTcM), (unsigned)((N + bn - 1) / bn));
+  k_gemm_bf16<<<grid, kGemmThreads, gemm_smem_bytes(bn), s>>>(ta, tb, C, N, K, ldc, bn, vec4,
+                                                              epi, err);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- the network's kernels
+constexpr int kIn = 7, kInP = 16, kHid = 256, kOut = 192;
+constexpr int kNParams = kHid * kIn + kHid + kHid * kHid + kHid + kOut * kHid + kOut;
+
 // x [B x 7] FP32 (rows >= n zero) -> X [Bp x 16] BF16 and its transpose [16 x Bp]
 __global__ void k_pack_input(const float* __restrict__ x, int n, int Bp, __nv_bfloat16* X,
                              __nv_bfloat16* Xt) {
@@ -132,27 +298,6 @@ __global__ void k_pack_input(const float* __restrict__ x, int n, int Bp, __nv_bf
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   X[i] = h;
   Xt[(size_t)k * Bp + b] = h;
-}
-
-// Z = C + bias; H = GELU(Z) as BF16, row-major and transposed ([N x Bp]); Z kept for backward
-__global__ void k_bias_gelu(const float* __restrict__ Cm, const float* __restrict__ bias, int Bp,
-                            int N, float* Z, __nv_bfloat16* H, __nv_bfloat16* Ht) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Bp * N) return;
-  const int b = i / N, j = i - b * N;
-  const float z = Cm[i] + bias[j];
-  if (Z) Z[i] = z;
-  const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
-  H[i] = h;
-  if (Ht) Ht[(size_t)j * Bp + b] = h;
-}
-
-// Y = C + bias (the linear output layer)
-__global__ void k_bias_out(const float* __restrict__ Cm, const float* __restrict__ bias, int n,
-                           int N, float* Y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * N) return;
-  Y[i] = Cm[i] + bias[i % N];
 }
 
 // Mean-squared error over B x N and its gradient dY = 2 (Y - T) / (B N): FP32, BF16 row-major
@@ -180,19 +325,6 @@ __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T,
     __syncthreads();
   }
   if (threadIdx.x == 0) rowloss[b] = red[0];
-}
-
-// dZ = dH * GELU'(Z): FP32 (for the bias gradient), BF16 row-major and transposed
-__global__ void k_gelu_back(const float* __restrict__ dH, const float* __restrict__ Z, int B,
-                            int N, float* dZ, __nv_bfloat16* dZh, __nv_bfloat16* dZt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * N) return;
-  const int b = i / N, j = i - b * N;
-  const float g = dH[i] * gelu_grad(Z[i]);
-  dZ[i] = g;
-  const __nv_bfloat16 h = __float2bfloat16_rn(g);
-  if (dZh) dZh[i] = h;
-  dZt[(size_t)j * B + b] = h;
 }
 
 // Column sums (bias gradients), one thread per column, rows in order (deterministic)
@@ -266,7 +398,7 @@ struct pic_mlp {
   float *P, *M, *V;  // parameters and Adam moments, flat layout
   __nv_bfloat16 *W1h, *W2h, *W2t, *W3h, *W3t;
   __nv_bfloat16 *Xh, *Xt, *H1h, *H1t, *H2h, *H2t, *dYh, *dYt, *dZh, *dZt;
-  float *Cb, *Z1, *Z2, *Y, *dY, *dH, *dZ, *gW1, *gW2t, *gW3t, *gb1, *gb2, *gb3;
+  float *Z1, *Z2, *Y, *dY, *dZ, *gW1, *gW2t, *gW3t, *gb1, *gb2, *gb3;
   double* rowloss;
   int* err;
 };
@@ -295,12 +427,10 @@ void mlp_carve(pic_mlp* m, char* base, int bmax, size_t* total) {
   m->dYt = c.take<__nv_bfloat16>(B * kOut);
   m->dZh = c.take<__nv_bfloat16>(B * kHid);
   m->dZt = c.take<__nv_bfloat16>(B * kHid);
-  m->Cb = c.take<float>(B * kHid);
   m->Z1 = c.take<float>(B * kHid);
   m->Z2 = c.take<float>(B * kHid);
   m->Y = c.take<float>(B * kOut);
   m->dY = c.take<float>(B * kOut);
-  m->dH = c.take<float>(B * kHid);
   m->dZ = c.take<float>(B * kHid);
   m->gW1 = c.take<float>((size_t)kHid * kInP);
   m->gW2t = c.take<float>((size_t)kHid * kHid);
@@ -325,25 +455,36 @@ cudaError_t mlp_refresh_bf16(pic_mlp* m) {
   return cudaGetLastError();
 }
 
-// Forward pass of n inputs x [n x 7] (device) into m->Y [n x 192]; Bp = n rounded up to 128
+// Forward pass of n inputs x [n x 7] (device) into m->Y [n x 192]; Bp = n rounded up to 128.
+// Bias and GELU run in the GEMM epilogues.
 cudaError_t mlp_forward(pic_mlp* m, const float* x, int n, int Bp) {
   cudaStream_t s = m->stream;
   k_pack_input<<<blocks((long long)Bp * kInP), 256, 0, s>>>(x, n, Bp, m->Xh, m->Xt);
-  cudaError_t e = launch_gemm(m->Xh, m->W1h, m->Cb, Bp, kHid, kInP, kHid, m->err, s);
+  GemmEpi h1;
+  h1.mode = kEpiBiasGelu;
+  h1.ldt = Bp;
+  h1.bias = m->P + kOffB1;
+  h1.Z = m->Z1;
+  h1.H = m->H1h;
+  h1.Ht = m->H1t;
+  cudaError_t e = launch_gemm(m->Xh, m->W1h, nullptr, Bp, kHid, kInP, kHid, m->err, s, h1);
   if (e != cudaSuccess) return e;
-  k_bias_gelu<<<blocks((long long)Bp * kHid), 256, 0, s>>>(m->Cb, m->P + kOffB1, Bp, kHid, m->Z1,
-                                                          m->H1h, m->H1t);
-  e = launch_gemm(m->H1h, m->W2h, m->Cb, Bp, kHid, kHid, kHid, m->err, s);
+  GemmEpi h2 = h1;
+  h2.bias = m->P + kOffB2;
+  h2.Z = m->Z2;
+  h2.H = m->H2h;
+  h2.Ht = m->H2t;
+  e = launch_gemm(m->H1h, m->W2h, nullptr, Bp, kHid, kHid, kHid, m->err, s, h2);
   if (e != cudaSuccess) return e;
-  k_bias_gelu<<<blocks((long long)Bp * kHid), 256, 0, s>>>(m->Cb, m->P + kOffB2, Bp, kHid, m->Z2,
-                                                          m->H2h, m->H2t);
-  e = launch_gemm(m->H2h, m->W3h, m->Cb, Bp, kOut, kHid, kOut, m->err, s);
-  if (e != cudaSuccess) return e;
-  k_bias_out<<<blocks((long long)n * kOut), 256, 0, s>>>(m->Cb, m->P + kOffB3, n, kOut, m->Y);
-  return cudaGetLastError();
+  GemmEpi out;
+  out.mode = kEpiBias;
+  out.rows = n;
+  out.bias = m->P + kOffB3;
+  return launch_gemm(m->H2h, m->W3h, m->Y, Bp, kOut, kHid, kOut, m->err, s, out);
 }
 
-// Loss and gradients of a batch of B (a multiple of 128) after mlp_forward(x, B, B)
+// Loss and gradients of a batch of B (a multiple of 128) after mlp_forward(x, B, B); the
+// GELU derivative runs in the epilogues of the dH products.
 cudaError_t mlp_backward(pic_mlp* m, const float* t, int B) {
   cudaStream_t s = m->stream;
   k_loss<<<B, 256, 0, s>>>(m->Y, t, B, kOut, m->dY, m->dYh, m->dYt, m->rowloss);
@@ -351,20 +492,25 @@ cudaError_t mlp_backward(pic_mlp* m, const float* t, int B) {
   cudaError_t e = launch_gemm(m->H2t, m->dYt, m->gW3t, kHid, kOut, B, kOut, m->err, s);
   if (e != cudaSuccess) return e;
   k_colsum<<<1, kOut, 0, s>>>(m->dY, B, kOut, m->gb3);
-  // dH2 = dY W3
-  e = launch_gemm(m->dYh, m->W3t, m->dH, B, kHid, kOut, kHid, m->err, s);
+  // dZ2 = (dY W3) GELU'(Z2)
+  GemmEpi g2;
+  g2.mode = kEpiGeluGrad;
+  g2.ldt = B;
+  g2.Zin = m->Z2;
+  g2.H = m->dZh;
+  g2.Ht = m->dZt;
+  e = launch_gemm(m->dYh, m->W3t, m->dZ, B, kHid, kOut, kHid, m->err, s, g2);
   if (e != cudaSuccess) return e;
-  k_gelu_back<<<blocks((long long)B * kHid), 256, 0, s>>>(m->dH, m->Z2, B, kHid, m->dZ, m->dZh,
-                                                         m->dZt);
   // dW2^T = H1^T dZ2
   e = launch_gemm(m->H1t, m->dZt, m->gW2t, kHid, kHid, B, kHid, m->err, s);
   if (e != cudaSuccess) return e;
   k_colsum<<<1, kHid, 0, s>>>(m->dZ, B, kHid, m->gb2);
-  // dH1 = dZ2 W2
-  e = launch_gemm(m->dZh, m->W2t, m->dH, B, kHid, kHid, kHid, m->err, s);
+  // dZ1 = (dZ2 W2) GELU'(Z1)
+  GemmEpi g1 = g2;
+  g1.Zin = m->Z1;
+  g1.H = nullptr;
+  e = launch_gemm(m->dZh, m->W2t, m->dZ, B, kHid, kHid, kHid, m->err, s, g1);
   if (e != cudaSuccess) return e;
-  k_gelu_back<<<blocks((long long)B * kHid), 256, 0, s>>>(m->dH, m->Z1, B, kHid, m->dZ, nullptr,
-                                                         m->dZt);
   // dW1 [256 x 16] = dZ1^T X
   e = launch_gemm(m->dZt, m->Xt, m->gW1, kHid, kInP, B, kInP, m->err, s);
   if (e != cudaSuccess) return e;
@@ -400,6 +546,8 @@ extern "C" {
 int pic_tc_gemm_bf16(const uint16_t* a, const uint16_t* b, float* c, int32_t m, int32_t n,
                      int32_t k, void* cuda_stream) {
   if (!a || !b || !c || !gemm_shape_ok(m, n, k)) return PIC_ERR_PARAM;
+  if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) != 0)
+    return PIC_ERR_PARAM;
   int* err = nullptr;
   const int zero = 0;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

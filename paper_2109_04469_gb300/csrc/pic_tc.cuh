@@ -51,6 +51,19 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// 2-D tiled tensor copy global -> shared (TMA) completing on `bar`: the box of the tensor map
+// `map` whose first element is (x, y), x counted in elements along the contiguous dimension
+// (x times the element size must be a multiple of 16 bytes); box parts outside the tensor are
+// zero-filled.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
 __device__ __forceinline__ void tc_mma_bf16(unsigned dtmem, unsigned long long adesc,
                                             unsigned long long bdesc, unsigned idesc,

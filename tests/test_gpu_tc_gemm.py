@@ -18,8 +18,14 @@ def _built():
     assert torch.cuda.is_available()
 
 
+# shapes of the network's products (forward at batch 1024, weight gradients with K = batch),
+# K tails shorter than a 64-wide stage, N tails shorter than a column tile, N above 256 (several
+# column tiles), and more K-stages than the ring holds
 @pytest.mark.parametrize("m,n,k", [(128, 16, 16), (128, 256, 256), (256, 192, 256),
-                                   (256, 256, 16), (384, 48, 80), (128, 128, 1024)])
+                                   (256, 256, 16), (384, 48, 80), (128, 128, 1024),
+                                   (1024, 256, 256), (1024, 192, 256), (1024, 256, 16),
+                                   (256, 16, 1024), (256, 192, 1024), (128, 208, 64),
+                                   (256, 640, 144), (128, 32, 2048)])
 def test_gemm_matches_float64(m, n, k):
     g = torch.Generator().manual_seed(m * 7 + n * 3 + k)
     a = torch.randn(m, k, generator=g).to(torch.bfloat16)
@@ -39,3 +45,16 @@ def test_bad_shapes_are_rejected():
     c = torch.zeros(100, 16, dtype=torch.float32, device="cuda")
     with pytest.raises(pic.PicError):  # m not a multiple of 128
         pic.tc_gemm_bf16(a, b, c)
+
+
+def test_misaligned_operand_is_rejected():
+    """The TMA tensor maps need 16-byte aligned operands: an offset view is refused on the
+    host, before any launch, and c is left untouched."""
+    base = torch.zeros(128 * 16 + 1, dtype=torch.bfloat16, device="cuda")
+    a = base[1:].view(128, 16)  # 2 bytes past a 256-byte boundary
+    b = torch.zeros(16, 16, dtype=torch.bfloat16, device="cuda")
+    c = torch.full((128, 16), 7.0, dtype=torch.float32, device="cuda")
+    with pytest.raises(pic.PicError) as e:
+        pic.tc_gemm_bf16(a, b, c)
+    assert e.value.code == -1
+    assert bool(torch.all(c == 7.0))
