@@ -346,6 +346,9 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   K.rfac = d.rfac;
   K.den1 = d.dx * (double)nc;  // N dx and 2 N dx of the field solve (reading C-23)
   K.den2 = (2.0 * d.dx) * (double)nc;
+  K.rden1 = 1.0 / K.den1;
+  K.rden2 = 1.0 / K.den2;
+  K.rnc = 1.0 / (double)nc;
   K.half_L = 0.5 * p->gap_m;
   K.half_dx = 0.5 * d.dx;
   K.qm_dt[0] = d.qm_dt[0];
@@ -416,9 +419,10 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   const long long by_size = (p->capacity_per_species + 255) / 256;
   h->push_grid = (int)std::max(1LL, std::min<long long>({(long long)sms * bps, by_size,
                                                           max_list_blocks(*p) / 8}));
-  h->place_grid = 1 + sms;
-  // hole / birth list owners: particle blocks (FP64 pass) or their warps (FP32 pass)
-  K.nlist = fp32 ? h->push_grid * (kBlock / 32) : h->push_grid;
+  K.nfield = place_field_blocks(nx);
+  h->place_grid = K.nfield + sms;
+  // hole / birth list owners: the particle blocks (the FP32 pass packs its warps' lists)
+  K.nlist = h->push_grid;
   set_list_counts(K, K.nlist);
   h->K = K;
   if ((fp32 ? configure_place_fp32(nx, K.nlist) : configure_place_fp64(nx, K.nlist)) !=

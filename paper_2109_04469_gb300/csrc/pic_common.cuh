@@ -166,10 +166,16 @@ __device__ __forceinline__ void block_scan_i128x2(__int128& a, __int128& b, __in
 //   E_j = (2V + rfac (S_{j-1} - S_{j+1})) / (2 N dx)   inside,
 //   E_0 = (V - rfac (S_1 + N dC_0)) / (N dx),  E_N = (V + rfac (S_{N-1} + N dC_N)) / (N dx)
 // (half-cell Gauss law at the electrodes, reading C-4).  Each value rounds once, so the
-// result is independent of the thread count.  Writes the FP64 field, and its FP32 copy in
-// cell units per step squared when K.fE is set.  smem: 16 * nx bytes.
+// result is independent of the thread count and of how the nodes are split over blocks.
+// Writes the FP64 field of nodes [jlo, jhi) (all nodes when jhi < 0), and its FP32 copy in
+// cell units per step squared when K.fE is set; the exact sums S_j are formed for every node.
+// With `mul` the three divisions become products with the reciprocals K.rden1, K.rden2, K.rnc
+// (within an ulp of FP64, and far cheaper on a part with a low FP64 rate): for the FP32
+// particle path, whose kicks are FP32; the FP64 path divides, as the oracle does.
+// smem: 16 * nx bytes.
 __device__ __forceinline__ void field_solve(const DevCtx& K, unsigned step, int buf,
-                                            void* smem) {
+                                            void* smem, int jlo = 0, int jhi = -1,
+                                            bool mul = false) {
   const int N = K.nc, nx = K.nx;
   __int128* Sg = reinterpret_cast<__int128*>(smem);
   const unsigned long long* Ce = K.C + (size_t)(buf * 2 + 0) * nx;
@@ -195,22 +201,27 @@ __device__ __forceinline__ void field_solve(const DevCtx& K, unsigned step, int 
     Sg[j] = (__int128)(N - j) * sa + (__int128)j * (tb - sb);
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+  if (jhi < 0) jhi = nx;
+  for (int j = jlo + (int)threadIdx.x; j < jhi; j += blockDim.x) {
     double e, ph;
     if (j == 0) {
       const __int128 q = Sg[1] + (__int128)N * (__int128)((long long)Ci[0] - (long long)Ce[0]);
-      e = __ddiv_rn(__dsub_rn(V, __dmul_rn(K.rfac, i128_to_f64(q))), K.den1);
+      const double a = __dsub_rn(V, __dmul_rn(K.rfac, i128_to_f64(q)));
+      e = mul ? __dmul_rn(a, K.rden1) : __ddiv_rn(a, K.den1);
       ph = V;
     } else if (j == N) {
       const __int128 q =
           Sg[N - 1] + (__int128)N * (__int128)((long long)Ci[N] - (long long)Ce[N]);
-      e = __ddiv_rn(__dadd_rn(V, __dmul_rn(K.rfac, i128_to_f64(q))), K.den1);
+      const double a = __dadd_rn(V, __dmul_rn(K.rfac, i128_to_f64(q)));
+      e = mul ? __dmul_rn(a, K.rden1) : __ddiv_rn(a, K.den1);
       ph = 0.0;
     } else {
-      e = __ddiv_rn(__dadd_rn(__dmul_rn(2.0, V), __dmul_rn(K.rfac, i128_to_f64(Sg[j - 1] - Sg[j + 1]))),
-                    K.den2);
-      ph = __ddiv_rn(__dadd_rn(__dmul_rn(V, (double)(N - j)), __dmul_rn(K.rfac, i128_to_f64(Sg[j]))),
-                     (double)N);
+      const double a =
+          __dadd_rn(__dmul_rn(2.0, V), __dmul_rn(K.rfac, i128_to_f64(Sg[j - 1] - Sg[j + 1])));
+      const double b =
+          __dadd_rn(__dmul_rn(V, (double)(N - j)), __dmul_rn(K.rfac, i128_to_f64(Sg[j])));
+      e = mul ? __dmul_rn(a, K.rden2) : __ddiv_rn(a, K.den2);
+      ph = mul ? __dmul_rn(b, K.rnc) : __ddiv_rn(b, (double)N);
     }
     K.E[j] = e;
     K.phi[j] = ph;
@@ -232,22 +243,26 @@ __device__ __forceinline__ void snapshot_pass(const DevCtx& K, unsigned step, lo
   K.st->id_snap[1] = K.st->next_id[1];
 }
 
-// Block 0 of the placement launch: close step n's accumulation (acc += C(n), counted),
-// clear that buffer for the deposit of step n+1, solve the field of step n+1, advance the
-// step index.
-__device__ __forceinline__ void advance_field(const DevCtx& K, void* smem) {
+// Field block f of F in the placement launch (F = 1: the whole grid): close step n's
+// accumulation (acc += C(n), counted) on its share of the nodes and clear that buffer for the
+// deposit of step n+1, solve the field of step n+1 on the same share (every field block forms
+// the exact sums of all nodes, so no block waits on another); block 0 advances the step index.
+// The counts read (step n+1's deposit) and the buffer cleared (step n's) are different.
+__device__ __forceinline__ void advance_field(const DevCtx& K, void* smem, int f = 0, int F = 1,
+                                              bool mul = false) {
   const unsigned m = K.st->step_next;  // n + 1
   const int done = (m - 1u) & 1u;      // buffer of step n
   const int nx = K.nx;
+  const int jlo = (int)((long long)nx * f / F), jhi = (int)((long long)nx * (f + 1) / F);
   unsigned long long* Cd = K.C + (size_t)(done * 2) * nx;
-  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+  for (int j = jlo + (int)threadIdx.x; j < jhi; j += blockDim.x) {
     K.acc[j] += (double)(long long)Cd[j];
     K.acc[nx + j] += (double)(long long)Cd[nx + j];
     Cd[j] = 0ull;
     Cd[nx + j] = 0ull;
   }
-  field_solve(K, m, m & 1u, smem);
-  if (threadIdx.x == 0) {
+  field_solve(K, m, m & 1u, smem, jlo, jhi, mul);
+  if (f == 0 && threadIdx.x == 0) {
     K.st->steps_avg += 1;
     K.st->step = m;
   }
@@ -368,42 +383,70 @@ __device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, Comp
   }
   if (threadIdx.x < 2) sq[threadIdx.x] = 0;
   __syncthreads();
-  const int seg = (G + NT - 1) / NT;
-  const int c0 = min((int)threadIdx.x * seg, G), c1 = min(c0 + seg, G);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int loc[kA], inc[kA];
+  if (G <= 32 * 32 && NW >= kA) {
+    // up to 1024 owners: one warp per array, 32 lanes over contiguous segments, one warp
+    // scan of the segment sums; one barrier before list 3 continues list 2's ranks
+    const int per = (G + 31) >> 5;
+    const int c0 = min(lane * per, G), c1 = min(c0 + per, G);
+    int loc = 0, inc = 0;
+    if (w < kA) {
+      for (int c = c0; c < c1; ++c) loc += sp[w * Gp + c];
+      inc = loc;
 #pragma unroll
-  for (int a = 0; a < kA; ++a) {
-    loc[a] = 0;
-    for (int c = c0; c < c1; ++c) loc[a] += sp[a * Gp + c];
-    inc[a] = loc[a];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) wtot[w] = inc;
+    }
+    __syncthreads();
+    if (w < kA) {
+      int run = inc - loc + (w == 3 ? wtot[2] : 0);
+      for (int c = c0; c < c1; ++c) {
+        const int v = sp[w * Gp + c];
+        sp[w * Gp + c] = run;
+        run += v;
+      }
+    }
+  } else {
+    const int seg = (G + NT - 1) / NT;
+    const int c0 = min((int)threadIdx.x * seg, G), c1 = min(c0 + seg, G);
+    int loc[kA], inc[kA];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, inc[a], o);
-      if (lane >= o) inc[a] += y;
-    }
-    if (lane == 31) wsum[w][a] = inc[a];
-  }
-  __syncthreads();
-  if (threadIdx.x < kA) {  // serial over the few warp sums
-    int run = 0;
-    for (int ww = 0; ww < NW; ++ww) {
-      const int v = wsum[ww][threadIdx.x];
-      wsum[ww][threadIdx.x] = run;
-      run += v;
-    }
-    wtot[threadIdx.x] = run;
-  }
-  __syncthreads();
+    for (int a = 0; a < kA; ++a) {
+      loc[a] = 0;
+      for (int c = c0; c < c1; ++c) loc[a] += sp[a * Gp + c];
+      inc[a] = loc[a];
 #pragma unroll
-  for (int a = 0; a < kA; ++a) {
-    int run = wsum[w][a] + inc[a] - loc[a] + (a == 3 ? wtot[2] : 0);
-    for (int c = c0; c < c1; ++c) {
-      const int v = sp[a * Gp + c];
-      sp[a * Gp + c] = run;
-      run += v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc[a], o);
+        if (lane >= o) inc[a] += y;
+      }
+      if (lane == 31) wsum[w][a] = inc[a];
+    }
+    __syncthreads();
+    if (threadIdx.x < kA) {  // serial over the few warp sums
+      int run = 0;
+      for (int ww = 0; ww < NW; ++ww) {
+        const int v = wsum[ww][threadIdx.x];
+        wsum[ww][threadIdx.x] = run;
+        run += v;
+      }
+      wtot[threadIdx.x] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < kA; ++a) {
+      int run = wsum[w][a] + inc[a] - loc[a] + (a == 3 ? wtot[2] : 0);
+      for (int c = c0; c < c1; ++c) {
+        const int v = sp[a * Gp + c];
+        sp[a * Gp + c] = run;
+        run += v;
+      }
     }
   }
+  __syncthreads();  // the prefixes are complete before any thread reads another's
   const int H2[2] = {wtot[0], wtot[1]};
   const int B2[2] = {wtot[2] + wtot[3], wtot[4]};
   // holes below Nn (needed when tail survivors fill holes): prefix of the owner of Nn plus
@@ -534,23 +577,27 @@ __device__ __forceinline__ void place_items(const DevCtx& K, int G, const int* s
   }
 }
 
-// Placement launch: block 0 advances the field; the other blocks each total the lists and
-// place the births and tail survivors; block 1 publishes the new counts and id counters.
+// Placement launch: blocks [0, K.nfield) advance the field, each on its share of the nodes;
+// the other blocks each total the lists and place the births and tail survivors; the first of
+// them publishes the new counts and id counters.
 template <class P>
 __global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
   extern __shared__ __align__(16) unsigned char place_smem[];
   chain_release();  // the next particle pass may take the SM room this launch leaves
   chain_wait();     // the particle pass of this step has completed
-  if (blockIdx.x == 0) {
-    advance_field(K, place_smem);
+  const int F = K.nfield;
+  if ((int)blockIdx.x < F) {
+    advance_field(K, place_smem, blockIdx.x, F, P::kFieldMul);
     return;
   }
   __shared__ CompactTot sT[2];
   int* sp = reinterpret_cast<int*>(place_smem);
   list_prefixes<256>(K, K.nlist, K.nlist, sp, sT);
-  if (blockIdx.x == 1 && threadIdx.x < 2) publish_counts(K, threadIdx.x, sT[threadIdx.x]);
-  place_items<P>(K, K.nlist, sp, sT, (long long)(blockIdx.x - 1) * blockDim.x + threadIdx.x,
-                 place_count(sT), (long long)(gridDim.x - 1) * blockDim.x);
+  const int b = blockIdx.x - F;
+  if (b == 0 && threadIdx.x < 2) publish_counts(K, threadIdx.x, sT[threadIdx.x]);
+  place_items<P>(K, K.nlist, sp, sT, (long long)b * blockDim.x + threadIdx.x, place_count(sT),
+                 (long long)(gridDim.x - F) * blockDim.x);
 }
+
 
 }  // namespace pic

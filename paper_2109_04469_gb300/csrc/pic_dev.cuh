@@ -62,6 +62,13 @@ __host__ __device__ __forceinline__ int range_owner(long long n, long long t, in
   return (int)b;
 }
 
+// Field blocks of the placement launch: about 64 nodes each (the FP64 divisions of a node
+// set are what one block spends its time on), at most 16.
+__host__ __device__ __forceinline__ int place_field_blocks(int nx) {
+  const int f = (nx + 63) / 64;
+  return f < 1 ? 1 : (f > 16 ? 16 : f);
+}
+
 // Device-resident scalars that change every step.
 struct DevState {
   long long n[2];       // live particles per species
@@ -106,6 +113,7 @@ struct DevCtx {
   int nc, nx, steps_per_rf, eepf_bins, fedf_bins, nchunk_max;
   long long cap;
   double L, dx, inv_dx, inv_2dx, dt, efac, rfac, den1, den2, half_L, half_dx;
+  double rden1, rden2, rnc;  // 1 / den1, 1 / den2, 1 / N: the FP32 path's field multiplies
   double qm_dt[2], emfac_e, spd2_e, emfac_rel, spd2_rel, emfac_ilab, mr2, sig_i, v_see;
   double sig_load[2];
   double pmax[2], refl, gamma, eepf_inv_de, fedf_inv_de;
@@ -129,6 +137,7 @@ struct DevCtx {
   // start at the slot of its first particle and are in particle order.  The counts are per
   // owner ([nlist] entries); the placement launch forms their prefixes in shared memory.
   int nlist;            // list owners of the particle pass
+  int nfield;           // field blocks of the placement launch
   int *hole_idx[2];     // [cap]: hole indices
   int *hole_cnt[2];
   int *eb_cnt[2];       // electron births from owners' species-s ranges

@@ -356,8 +356,11 @@ struct PipeCount {         // per-warp, warp-uniform, in registers
 
 __device__ __forceinline__ unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
 
-__device__ __forceinline__ bool in_eepf_cells(const DevCtx* __restrict__ G, int cell) {
-  return (unsigned)(cell - G->eepf_jlo) <= (unsigned)(G->eepf_jhi - G->eepf_jlo);
+// The cells an electron of the EEPF window |x / dx - N / 2| < 1/2 can sit in: (N - 1) / 2 to
+// N / 2.  With the offset in [0, 1] (renorm can round it up to 1) and the cell a small integer,
+// the window test of eepf32 is exact in FP32 and fails in every other cell.
+__device__ __forceinline__ bool in_eepf_cells(int nc, int cell) {
+  return (unsigned)(cell - (nc - 1) / 2) <= (unsigned)(nc / 2 - (nc - 1) / 2);
 }
 
 // Handle the first n queued entries (n <= 32, of nq queued), one per lane, in queue order
@@ -385,7 +388,7 @@ __device__ __noinline__ int drain32(const DevCtx* __restrict__ G, unsigned step,
       born = o.born != 0;
       vx = o.vx;
     }
-    if (S == 0 && in_eepf_cells(G, cell)) eepf32(G, c.p, cell, c.off, vx, sCnt);
+    if (S == 0 && in_eepf_cells(G->nc, cell)) eepf32(G, c.p, cell, c.off, vx, sCnt);
   }
   int nb = 0;
   if (S == 0) {
@@ -527,7 +530,7 @@ __device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long
         const bool ex = (cd[j] & 0x7FFFu) == 0u;
         expm |= (unsigned)ex << j;
         deposit32(S == 0 ? sCe : sCi, cell[j], off[j]);
-        if (S == 0 && !ex && in_eepf_cells(G, cell[j])) eepm |= 1u << j;
+        if (S == 0 && !ex && in_eepf_cells(nc, cell[j])) eepm |= 1u << j;
       }
     }
     if (nv == 128) {
@@ -588,13 +591,16 @@ __device__ __forceinline__ void flush32(const DevCtx& K, unsigned* sC, unsigned 
 }
 
 // Species S for the whole block: each warp its own range, in rounds that bound the 32-bit
-// counters.
+// counters.  The warp's list lengths go to wc[list][warp] (lists: 0, 1 holes of electrons /
+// ions; 2, 3 electron births from electron / ion ranges; 4 ion births), its first particle of
+// species S to wb[S][warp].
 template <int S>
 __device__ __forceinline__ void block_pass32(const DevCtx& K, unsigned step, long long n,
                                              const float2* sE, unsigned* sC,
                                              unsigned long long* sCnt, unsigned long long* Cn,
-                                             WarpPipe& P, PipeCount& Q) {
-  const int GW = K.nlist;  // warps of the grid
+                                             WarpPipe& P, PipeCount& Q, int (*wc)[kWarps32],
+                                             long long (*wb)[kWarps32]) {
+  const int GW = gridDim.x * kWarps32;  // warps of the grid
   const int gw = blockIdx.x * kWarps32 + (threadIdx.x >> 5);
   const long long q0 = range_begin(n, gw, GW), q1 = range_begin(n, gw + 1, GW);
   long long hk = q0, ek = q0, ik = q0;  // list slots of this warp
@@ -614,10 +620,134 @@ __device__ __forceinline__ void block_pass32(const DevCtx& K, unsigned step, lon
     if (r + 1 < rounds) flush32(K, sC, Cn);
   }
   if ((threadIdx.x & 31) == 0) {
-    K.hole_cnt[S][gw] = (int)(hk - q0);
-    K.eb_cnt[S][gw] = (int)(ek - q0);
-    if (S == 0) K.ib_cnt[gw] = (int)(ik - q0);
+    const int w = threadIdx.x >> 5;
+    wb[S][w] = q0;
+    wc[S][w] = (int)(hk - q0);
+    wc[2 + S][w] = (int)(ek - q0);
+    if (S == 0) wc[4][w] = (int)(ik - q0);
   }
+}
+
+// The lists of the block's warps, each written from its warp's first particle on, packed into
+// one list per block from the block's first particle on (warp b 8 + w of the grid's warps
+// starts where block b starts for w = 0; the block's range is the union of its warps'), and
+// the block's list lengths in K.hole_cnt rows of stride gridDim.x.  Warp order is particle
+// order, so every list stays in particle order (reading C-15 ranks births and holes by it).
+// An entry only moves down (a warp lists at most one entry per particle of its range).  When
+// every destination lies below the first entry that moves (the usual case: a list is much
+// shorter than a warp's range), each warp moves its own entries with no further barrier;
+// otherwise the block moves them in rounds of one entry per thread -- every load of a round
+// before a barrier, every store after it -- so no store reaches an entry still to be loaded.
+// Called by the whole block after both species passes.
+__device__ void pack_block_lists(const DevCtx& K, const int (*wc)[kWarps32],
+                                 const long long (*wb)[kWarps32]) {
+  __shared__ int off[5][kWarps32 + 1];
+  __shared__ int direct[5];
+  const int G = gridDim.x, b = blockIdx.x;
+  const size_t cap = (size_t)K.nchunk_max * kChunk;
+  if (threadIdx.x < 5) {
+    const int a = threadIdx.x, sp = (a == 1 || a == 3) ? 1 : 0;
+    int run = 0, first = -1;
+    for (int w = 0; w < kWarps32; ++w) {
+      off[a][w] = run;
+      if (w > 0 && first < 0 && wc[a][w] > 0) first = w;
+      run += wc[a][w];
+    }
+    off[a][kWarps32] = run;
+    direct[a] = first < 0 || wb[sp][0] + run <= wb[sp][first];
+  }
+  __syncthreads();
+  if (direct[0] & direct[1] & direct[2] & direct[3] & direct[4]) {
+    // each warp its own entries, 32 per round of every list: all loads, then all stores
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w == 0) goto counts;  // warp 0's entries are in place
+    {
+      int mmax = 0;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) mmax = max(mmax, off[a][w + 1] - off[a][w]);
+      for (int e0 = 0; e0 < mmax; e0 += 32) {
+        const int e = e0 + lane;
+        int hv[2];
+        float rv[3][6];
+        bool mv[5];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+          const int sp = (a == 1 || a == 3) ? 1 : 0;
+          mv[a] = e < off[a][w + 1] - off[a][w];
+          if (!mv[a]) continue;
+          const long long src = wb[sp][w] + e;
+          if (a < 2) {
+            hv[a] = K.hole_idx[a][src];
+          } else {
+            const float* rec = a == 2 ? K.feb[0] : (a == 3 ? K.feb[1] : K.fib);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rv[a - 2][k] = rec[src + k * cap];
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+          if (!mv[a]) continue;
+          const int sp = (a == 1 || a == 3) ? 1 : 0;
+          const long long dst = wb[sp][0] + off[a][w] + e;
+          if (a < 2) {
+            K.hole_idx[a][dst] = hv[a];
+          } else {
+            float* rec = a == 2 ? K.feb[0] : (a == 3 ? K.feb[1] : K.fib);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rec[dst + k * cap] = rv[a - 2][k];
+          }
+        }
+      }
+    }
+  counts:
+    if (threadIdx.x < 5) K.hole_cnt[0][(size_t)threadIdx.x * G + b] = off[threadIdx.x][kWarps32];
+    return;
+  }
+  int rounds = 0;
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+    rounds = max(rounds, (off[a][kWarps32] + (int)blockDim.x - 1) / (int)blockDim.x);
+  for (int r = 0; r < rounds; ++r) {
+    const int i = r * blockDim.x + threadIdx.x;
+    long long dst[5];
+    int hv[2];
+    float rv[3][6];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      dst[a] = -1;
+      if (i < off[a][kWarps32]) {
+        const int sp = (a == 1 || a == 3) ? 1 : 0;
+        int w = 0;
+        while (w + 1 < kWarps32 && off[a][w + 1] <= i) ++w;
+        const long long src = wb[sp][w] + (i - off[a][w]);
+        const long long d = wb[sp][0] + i;
+        if (src != d) {
+          dst[a] = d;
+          if (a < 2) {
+            hv[a] = K.hole_idx[a][src];
+          } else {
+            const float* rec = a == 2 ? K.feb[0] : (a == 3 ? K.feb[1] : K.fib);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rv[a - 2][k] = rec[src + k * cap];
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      if (dst[a] < 0) continue;
+      if (a < 2) {
+        K.hole_idx[a][dst[a]] = hv[a];
+      } else {
+        float* rec = a == 2 ? K.feb[0] : (a == 3 ? K.feb[1] : K.fib);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) rec[dst[a] + k * cap] = rv[a - 2][k];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) K.hole_cnt[0][(size_t)threadIdx.x * G + b] = off[threadIdx.x][kWarps32];
 }
 
 __host__ __device__ __forceinline__ size_t pipes_offset(int nx) {
@@ -652,16 +782,20 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
   if (blockIdx.x == 0 && threadIdx.x == 0) snapshot_pass(K, step, ne, ni);
   __syncthreads();
   unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
-  block_pass32<0>(K, step, ne, sE, sC, sCnt, Cn, P, Q);
+  __shared__ int wc[5][kWarps32];
+  __shared__ long long wb[2][kWarps32];
+  block_pass32<0>(K, step, ne, sE, sC, sCnt, Cn, P, Q, wc, wb);
   flush32(K, sC, Cn);
-  block_pass32<1>(K, step, ni, sE + nx, sC, sCnt, Cn, P, Q);
-  flush32(K, sC, Cn);
+  block_pass32<1>(K, step, ni, sE + nx, sC, sCnt, Cn, P, Q, wc, wb);
+  flush32(K, sC, Cn);  // ends with a block barrier: every warp's lists are complete
   if (threadIdx.x < kNumCounters && sCnt[threadIdx.x])
     atomicAdd(&K.counters[threadIdx.x], sCnt[threadIdx.x]);
+  pack_block_lists(K, wc, wb);
 }
 
 // Record moves of the FP32 representation for the placement launch.
 struct Fp32Moves {
+  static constexpr bool kFieldMul = true;  // FP32 kicks: the field solve multiplies
   // every field is loaded before the first store, so the loads are in flight together
   static __device__ __forceinline__ void birth(const DevCtx& K, int s, int list, long long slot,
                                                long long d, unsigned id) {
@@ -820,7 +954,7 @@ __device__ __noinline__ void ensemble_phase2(EnsDev* E, unsigned par, unsigned s
         c.nid = K.st->id_snap[sp];
         publish_counts(K, sp, c);
       }
-      advance_field(K, esm);
+      advance_field(K, esm, 0, 1, Fp32Moves::kFieldMul);
     }
     return;
   }

@@ -125,7 +125,8 @@ __global__ void k_max_abs(const double* __restrict__ v, long long n, unsigned lo
 __global__ void k_field(DevCtx K) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const unsigned step = K.st->step;
-  field_solve(K, step, step & 1, fsm);
+  // an FP32 particle state (K.fE set) takes the field in the form its steps use
+  field_solve(K, step, step & 1, fsm, 0, -1, K.fE[0] != nullptr);
 }
 
 // --------------------------------------------------------- one particle (§2 steps 3-6)
@@ -444,6 +445,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_push_fp64(DevCtx K) {
 
 // Record moves of the FP64 representation for the placement launch.
 struct Fp64Moves {
+  static constexpr bool kFieldMul = false;  // bit-exact with the oracle: the field solve divides
   // every field is loaded before the first store, so the loads are in flight together
   static __device__ __forceinline__ void birth(const DevCtx& K, int s, int list, long long slot,
                                                long long d, unsigned id) {
