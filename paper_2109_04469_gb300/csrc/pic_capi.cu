@@ -719,13 +719,22 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
   // max |vx| over the electrons for the CFL number
   PIC_CUDA(cudaMemsetAsync(&K.st->vmax_bits, 0, sizeof(unsigned long long), h->stream));
-  if (is_fp32(h)) PIC_CUDA(launch_convert(K, 0, s.n[0], false, h->stream));
-  PIC_CUDA(launch_max_abs(K.vx[0], s.n[0], &K.st->vmax_bits, h->stream));
+  if (is_fp32(h))  // straight from the FP32 state, in cells per step
+    PIC_CUDA(launch_max_abs_vx32(K, 0, s.n[0], &K.st->vmax_bits, h->stream));
+  else
+    PIC_CUDA(launch_max_abs(K.vx[0], s.n[0], &K.st->vmax_bits, h->stream));
   unsigned long long vbits = 0;
   PIC_CUDA(cudaStreamSynchronize(h->stream));
   PIC_CUDA(cudaMemcpy(&vbits, &K.st->vmax_bits, sizeof vbits, cudaMemcpyDeviceToHost));
   double vmax;
-  std::memcpy(&vmax, &vbits, sizeof vmax);
+  if (is_fp32(h)) {
+    float f;
+    const uint32_t b = (uint32_t)vbits;
+    std::memcpy(&f, &b, sizeof f);
+    vmax = (double)f * K.to_si_v;
+  } else {
+    std::memcpy(&vmax, &vbits, sizeof vmax);
+  }
 
   const Derived& d = h->d;
   const int64_t steps = s.steps_avg;

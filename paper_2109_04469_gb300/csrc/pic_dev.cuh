@@ -12,6 +12,7 @@ namespace pic {
 constexpr int kChunk = 1024;       // particles per chunk (hole / birth bookkeeping unit)
 constexpr int kBlock = 256;        // threads per block of the particle kernels
 constexpr int kTile = 2 * kBlock;  // particles per block-wide pass (two per thread)
+constexpr int kDepositBlocks = 304; // grid of the stand-alone deposits (shared counts per block)
 constexpr int kXsNodes = 100001;   // collision table nodes at eps_k = k / 100 eV
 constexpr double kXsInvDe = 100.0;
 constexpr int kMaxTries = 64;      // rejection-sampling attempts before the fixed fallback

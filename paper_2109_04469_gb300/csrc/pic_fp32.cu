@@ -24,6 +24,8 @@
 // EEPF samples) are out-of-line calls so the hot loop stays small.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pic_common.cuh"
 #include "pic_dev.cuh"
 #include "pic_launch.h"
@@ -839,6 +841,17 @@ __global__ void k_to_fp32(DevCtx K, int s, long long n) {
   K.ccd[s][q] = (unsigned)j | ((unsigned)draw_countdown(next_u(st), K.f_lnq[s]) << 16);
 }
 
+// max |vx| of the first n particles of species s in cells per step, as the bits of a float
+// (non-negative floats order like their bit patterns; a non-finite value wins)
+__global__ void k_max_abs_vx32(DevCtx K, int s, long long n, unsigned long long* out) {
+  unsigned m = 0u;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fabsf(K.ov[s][q].y)));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, (unsigned long long)m);
+}
+
 // FP32 cell units -> FP64 SI state, for pic_get_particles and the diagnostics.
 __global__ void k_to_fp64(DevCtx K, int s, long long n) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -852,13 +865,22 @@ __global__ void k_to_fp64(DevCtx K, int s, long long n) {
 
 // Deposit of the FP32 state with the FP32 rule (16-bit weights), after a load or a set.
 __global__ void k_deposit32(DevCtx K, int s, int buf, long long n) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const int j = (int)(K.ccd[s][q] & 0xFFFFu);
-  const int wr = __float2int_rn(K.ov[s][q].x * 65536.0f);
-  unsigned long long* C = K.C + (size_t)(buf * 2 + s) * K.nx;
-  atomicAdd(&C[j], (unsigned long long)(65536 - wr) << 16);
-  atomicAdd(&C[j + 1], (unsigned long long)wr << 16);
+  // block-private counts over a grid-stride loop, then one global atomic per touched node
+  extern __shared__ unsigned long long dsm32[];
+  const int nx = K.nx;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) dsm32[j] = 0ull;
+  __syncthreads();
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(K.ccd[s][q] & 0xFFFFu);
+    const int wr = __float2int_rn(K.ov[s][q].x * 65536.0f);
+    atomicAdd(&dsm32[j], (unsigned long long)(65536 - wr) << 16);
+    atomicAdd(&dsm32[j + 1], (unsigned long long)wr << 16);
+  }
+  __syncthreads();
+  unsigned long long* C = K.C + (size_t)(buf * 2 + s) * nx;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x)
+    if (dsm32[j]) atomicAdd(&C[j], dsm32[j]);
 }
 
 // ------------------------------------------------------------ ensemble (one launch a step)
@@ -1200,9 +1222,19 @@ cudaError_t launch_convert(const DevCtx& K, int species, long long n, bool to_fp
   return cudaGetLastError();
 }
 
+cudaError_t launch_max_abs_vx32(const DevCtx& K, int species, long long n,
+                                unsigned long long* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  k_max_abs_vx32<<<(unsigned)(want < 1024 ? want : 1024), 256, 0, s>>>(K, species, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_deposit32(const DevCtx& K, int species, int buf, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_deposit32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(K, species, buf, n);
+  const long long blocks = std::min<long long>((n + 255) / 256, kDepositBlocks);
+  k_deposit32<<<(unsigned)blocks, 256, sizeof(unsigned long long) * K.nx, s>>>(K, species, buf,
+                                                                              n);
   return cudaGetLastError();
 }
 

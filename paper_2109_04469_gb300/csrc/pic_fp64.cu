@@ -15,6 +15,8 @@
 // the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pic_common.cuh"
 #include "pic_dev.cuh"
 #include "pic_launch.h"
@@ -89,9 +91,19 @@ __global__ void k_init_load(DevCtx K, int s, long long n0) {
 }
 
 __global__ void k_deposit(DevCtx K, int s, int buf, long long n) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  deposit_to(K, K.C + (size_t)(buf * 2 + s) * K.nx, K.x[s][q]);
+  // block-private counts over a grid-stride loop, then one global atomic per touched node
+  // (integer sums, so the order of the additions does not matter)
+  extern __shared__ unsigned long long dsm[];
+  const int nx = K.nx;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) dsm[j] = 0ull;
+  __syncthreads();
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    deposit_to(K, dsm, K.x[s][q]);
+  __syncthreads();
+  unsigned long long* C = K.C + (size_t)(buf * 2 + s) * nx;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x)
+    if (dsm[j]) atomicAdd(&C[j], dsm[j]);
 }
 
 // Counts live in buffer (step & 1) and the other buffer must be zero (it receives the next
@@ -486,7 +498,8 @@ cudaError_t launch_init_load(const DevCtx& K, int species, long long n0, cudaStr
 cudaError_t launch_deposit(const DevCtx& K, int species, int buf, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int bs = 256;
-  k_deposit<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(K, species, buf, n);
+  const long long blocks = std::min<long long>((n + bs - 1) / bs, kDepositBlocks);
+  k_deposit<<<(unsigned)blocks, bs, sizeof(unsigned long long) * K.nx, s>>>(K, species, buf, n);
   return cudaGetLastError();
 }
 

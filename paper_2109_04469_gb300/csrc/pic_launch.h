@@ -19,6 +19,8 @@ cudaError_t launch_push_fp64(const DevCtx& K, int grid, cudaStream_t s);
 // accumulation, solves the field of the next step and advances the step index
 cudaError_t launch_place_fp64(const DevCtx& K, int grid, cudaStream_t s);
 cudaError_t launch_set_step(const DevCtx& K, unsigned step, cudaStream_t s);
+cudaError_t launch_max_abs_vx32(const DevCtx& K, int species, long long n,
+                                unsigned long long* out, cudaStream_t s);
 cudaError_t launch_max_abs(const double* v, long long n, unsigned long long* out,
                            cudaStream_t s);
 int push_fp64_blocks_per_sm(int nx);
