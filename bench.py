@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", default="ccp_1pa_300v_400c")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-stress", action="store_true")
+    ap.add_argument("--stress-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-ensemble", action="store_true")
@@ -363,6 +365,35 @@ def measure_ensemble(args, torch, dist, rank: int) -> dict:
     return out
 
 
+def measure_stress(args, torch, dist, local_rank: int, rank: int, peak: float) -> dict:
+    """The stress workload (5e7 + 5e7 superparticles, 1025 nodes): both precisions, the split
+    of a step between the particle launch, the placement launch and the field solve, and the
+    field solve's share of the step."""
+    import types
+
+    from paper_2109_04469_gb300 import workloads
+
+    name = "ccp_20pa_500v_1024c"
+    scfg = workloads.params(name)
+    scfg["instance"] = rank
+    sargs = types.SimpleNamespace(**vars(args))
+    sargs.steps, sargs.warmup = args.stress_steps, 3
+    out = {"workload": name + ": 3 cm, 1024 cells, 20 Pa, 500 V, N_t 4000, 5e7 + 5e7 "
+                              "superparticles, R 0.2, gamma 0.2",
+           "l2": "state of several GB, larger than L2 (the flush between steps is kept)"}
+    for prec in ("fp32", "fp64"):
+        r = measure(scfg, prec, sargs, torch, dist, local_rank, with_e2e=False)
+        t, p = reduce_ranks(torch, dist, r["step_ms"], r["parts"])
+        ms = t / sargs.steps
+        out[prec] = {"value": p / (t / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "particles_ms": r["push_ms"], "placement_and_next_field_ms": r["place_ms"],
+                     "field_alone_ms": r["field_ms"], "poisson_share": r["field_ms"] / ms,
+                     "roofline_frac_hbm": r["alg_bytes_per_launch"] / (r["push_ms"] / 1e3)
+                     / 1e9 / peak,
+                     "status": r["status"], "clocks": r["clocks"]}
+    return out
+
+
 def measure_surrogate(torch) -> dict:
     """The surrogate: a 384-setting scan run by the FP32 ensemble (half an RF
     period to warm up, half to average), the network trained on 320 settings by the
@@ -511,6 +542,8 @@ def main():
                            "births (counted), which is what a status of -3 reports"}
         if "fp64" in runs and "fp64" != head_prec:
             line["ensemble"]["speedup_vs_fp64_plain"] = ev / line["fp64_plain"]["value"]
+    if not args.no_stress:
+        line["stress"] = measure_stress(args, torch, dist, local_rank, rank, peak)
     if not args.no_surrogate and rank == 0:
         line["surrogate"] = measure_surrogate(torch)
     if "e2e" in head:

@@ -134,11 +134,14 @@ __global__ void k_max_abs(const double* __restrict__ v, long long n, unsigned lo
 
 // Stand-alone field solve for the current step (after init, set_particles, set_step, or on
 // request); touches no accumulator.
+// Block f of F writes nodes [nx f / F, nx (f + 1) / F), like the field blocks of a step.
 __global__ void k_field(DevCtx K) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const unsigned step = K.st->step;
+  const int F = gridDim.x, f = blockIdx.x, nx = K.nx;
+  const int jlo = (int)((long long)nx * f / F), jhi = (int)((long long)nx * (f + 1) / F);
   // an FP32 particle state (K.fE set) takes the field in the form its steps use
-  field_solve(K, step, step & 1, fsm, 0, -1, K.fE[0] != nullptr);
+  field_solve(K, step, step & 1, fsm, jlo, jhi, K.fE[0] != nullptr);
 }
 
 // --------------------------------------------------------- one particle (§2 steps 3-6)
@@ -504,7 +507,7 @@ cudaError_t launch_deposit(const DevCtx& K, int species, int buf, long long n, c
 }
 
 cudaError_t launch_field(const DevCtx& K, cudaStream_t s) {
-  k_field<<<1, 256, field_smem_bytes(K.nx), s>>>(K);
+  k_field<<<(unsigned)(K.nfield > 0 ? K.nfield : 1), 256, field_smem_bytes(K.nx), s>>>(K);
   return cudaGetLastError();
 }
 

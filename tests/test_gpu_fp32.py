@@ -165,6 +165,21 @@ def test_fp32_full_size_workload_runs():
     sim.close()
 
 
+def test_fp32_stress_workload_runs():
+    """The stress workload (5e7 + 5e7 superparticles, 1025 nodes) in FP32: bookkeeping stays
+    exact over a few steps and the populations stay in range."""
+    cfg = workloads.params("ccp_20pa_500v_1024c")
+    cfg["precision"] = pic.PIC_FP32
+    sim = pic.Simulation(cfg)
+    sim.step(3)
+    assert sim.sync() == 0
+    ne, ni = sim.counts()
+    g = sim.grid()
+    assert int(g["Ce"].sum()) == ne * 2**32 and int(g["Ci"].sum()) == ni * 2**32
+    assert 4.9e7 < ne < 5.1e7 and 4.9e7 < ni < 5.1e7
+    sim.close()
+
+
 def test_fp32_largest_grid_runs():
     """The largest grid the handles accept (4096 cells): shared-memory tables of 4097 nodes."""
     cfg = _cfg(n_cells=4096, init_per_species=20000, capacity_per_species=65536)
