@@ -83,6 +83,32 @@ def test_members_match_single_runs_bit_for_bit():
     ens.close()
 
 
+def test_crowded_lists_match_an_ensemble_member():
+    """A 2 mm gap with 2 keV electrons: nearly every electron leaves within the first steps,
+    so a particle block's hole list outgrows its first warp's range and the single run packs
+    its warps' lists in barrier-separated rounds.  The ensemble's owners need no packing, so
+    the two runs agree bit for bit only if the packed lists keep particle order."""
+    def cfg():
+        c = workloads.params("ccp_5pa_150v_128c", gap_m=0.002, init_te_ev=2000.0, refl_e=0.5,
+                             gamma_see=0.3, init_per_species=40000)
+        c.update(precision=pic.PIC_FP32, instance=9, capacity_per_species=60000)
+        return c
+
+    if not _STREAM:
+        _STREAM.append(torch.cuda.Stream())
+    with torch.cuda.stream(_STREAM[0]):
+        a, b = pic.Simulation(cfg()), pic.Simulation(cfg())
+    ens = pic.Ensemble([a], [10**9])
+    ens.step(6)
+    assert ens.sync() == 0
+    b.step(6)
+    assert b.sync() == 0
+    ne, _ = b.counts()
+    assert ne < 20000  # most electrons left: the lists were crowded
+    _same(a, b, "crowded")
+    ens.close()
+
+
 def test_uneven_targets_stop_each_member():
     targets = [60, 25, 0, 45]
     ens_sims, solo = _members(), _members()
