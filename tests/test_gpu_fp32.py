@@ -53,6 +53,19 @@ def test_fp32_initial_state_is_the_fp64_load_rounded():
     sim.close()
 
 
+def test_fp32_cfl_matches_fp64_at_load():
+    """pic_diag's CFL number comes straight from the FP32 velocities: at step 0 (the FP64 load
+    rounded) it equals the FP64 handle's to FP32 rounding."""
+    cfg = _cfg()
+    a = pic.Simulation(cfg)
+    cfg64 = dict(cfg, precision=pic.PIC_FP64)
+    b = pic.Simulation(cfg64)
+    ca, cb = a.diag()["cfl_max"], b.diag()["cfl_max"]
+    assert cb > 0 and abs(ca - cb) <= 2e-7 * cb, (ca, cb)
+    a.close()
+    b.close()
+
+
 def test_fp32_bookkeeping_exact():
     cfg = _cfg(refl_e=0.3, gamma_see=0.2)
     sim = pic.Simulation(cfg)
