@@ -395,7 +395,7 @@ def measure_stress(args, torch, dist, local_rank: int, rank: int, peak: float) -
 
 
 def measure_surrogate(torch) -> dict:
-    """The surrogate: a 384-setting scan run by the FP32 ensemble (half an RF
+    """The surrogate network of the parameter scans: a 384-setting scan run by the FP32 ensemble (half an RF
     period to warm up, half to average), the network trained on 320 settings by the
     tensor-core kernels, judged on the 64 held-out settings by the plain method's profiles;
     plus the tensor-core GEMM rate of its widest layer at batch 1024."""

@@ -13,6 +13,46 @@
  *  - Arrays passed to pic_get_* / pic_set_* / pic_diag are HOST arrays owned by the caller.
  *  - Units are SI unless a name says otherwise (_ev: electronvolt).
  *  - Species index: 0 = electrons, 1 = Ar+ ions.
+ *
+ * Readings of the paper used in these sources (where §2 leaves a detail open; comments cite
+ * them as "reading C-n"):
+ *  C-1  N_c cells, N_x = N_c + 1 nodes, dx = L / N_c.
+ *  C-2  Drive V(t_n) = V_rf cos(2 pi f n dt) on x = 0 at the start of step n; x = L grounded.
+ *  C-3  Loaded velocities are taken at n - 1/2 (no half-step push back).
+ *  C-4  Field at the electrodes from the half-cell Gauss law:
+ *       E_0 = (phi_0 - phi_1)/dx - rho_0 dx/(2 eps0), E_N = (phi_N-1 - phi_N)/dx + rho_N dx/(2 eps0).
+ *  C-5  An electrode node owns half a cell of volume.
+ *  C-7  One null-collision trial per particle and step: a candidate if u < P_max =
+ *       1 - exp(-nu_max dt).
+ *  C-8  nu_max is the largest total collision frequency over the cross-section table.
+ *  C-9  Electron elastic scattering: isotropic in the lab frame off a cold atom, with the
+ *       recoil loss of a fraction (2 m_e / M)(1 - cos chi) of the energy.
+ *  C-10 Ionization: the energy above threshold shared equally by the two electrons, both
+ *       isotropic; the new ion drawn from the gas Maxwellian.
+ *  C-11 An ion-induced electron starts at the struck electrode with see_energy_ev, isotropic
+ *       into the gap.
+ *  C-12 Absorbed iff x <= 0 or x >= L; a reflected electron has x mirrored and vx negated and
+ *       is removed if still outside.
+ *  C-13 Ar+ - Ar: isotropic scattering in the centre-of-mass frame, or charge transfer (the ion
+ *       takes the sampled atom's velocity).
+ *  C-14 Deposit in fixed point: 2^32 per superparticle, w_R = rint(f 2^32) (ties to even),
+ *       w_L = 2^32 - w_R.
+ *  C-15 Compaction: removed particles leave holes; births, ranked in particle order and given
+ *       ids next_id + rank, fill the holes in rank order and then follow the last particle;
+ *       survivors beyond the new count fill the holes that remain below it.
+ *  C-16 Random numbers: Philox4x32-10, key (seed, instance), counter (id, step,
+ *       species | purpose | block, 0).
+ *  C-18 EEPF: electrons with |x - L/2| < dx/2, sampled every step.
+ *  C-19 omega_pe and lambda_D from the time-averaged centre density and k T_e = (2/3) <eps>
+ *       of the centre EEPF.
+ *  C-20 N_D = n_e(L/2) A lambda_D / W, superparticles per Debye length.
+ *  C-21 Gamma = W x ions absorbed at an electrode / (A x time), the mean of both electrodes.
+ *  C-22 Initial load: x uniform in (0, L), Maxwellian velocities, ids 0 .. N-1.
+ *  C-23 The tridiagonal Poisson system solved exactly through its discrete Green's function in
+ *       integer arithmetic, each output value rounded once.
+ *  C-XS Closed-form cross sections (Phelps' tables are not available): electron elastic,
+ *       excitation at 11.55 eV, Lotz-type ionization at 15.76 eV; Ar+ - Ar isotropic and
+ *       charge transfer.
  */
 #ifndef PIC_H
 #define PIC_H
@@ -272,7 +312,7 @@ int pic_selftest_waits(void* workspace, size_t workspace_bytes, void* cuda_strea
                        int32_t* codes);
 
 /* ---------------------------------------------------------------------------------------
- * Surrogate network (the paper has none): BF16 tensor-core kernels.
+ * Surrogate network of the §3 parameter scans (the paper has none): BF16 tensor-core kernels.
  * --------------------------------------------------------------------------------------- */
 
 /* C[m x n] = A[m x k] * B[n x k]^T on the tcgen05 tensor cores: A, B DEVICE arrays of BF16

@@ -9,8 +9,48 @@
  * matters: contracted multiply-adds would change the rounding).
  *
  * Every routine cites the passage of the paper it follows.  Where the paper is silent the
- * project's readings (C-1 .. C-22, C-XS) are named.  Pins (tests that fix this code to
- * something other than itself) live in tests/test_oracle_*.py.
+ * reading it takes is named (listed below).  Pins (tests that fix this code to something
+ * other than itself) live in tests/test_oracle_*.py.
+ *
+ * Readings of the paper used in these sources (where §2 leaves a detail open; comments cite
+ * them as "reading C-n"):
+ *  C-1  N_c cells, N_x = N_c + 1 nodes, dx = L / N_c.
+ *  C-2  Drive V(t_n) = V_rf cos(2 pi f n dt) on x = 0 at the start of step n; x = L grounded.
+ *  C-3  Loaded velocities are taken at n - 1/2 (no half-step push back).
+ *  C-4  Field at the electrodes from the half-cell Gauss law:
+ *       E_0 = (phi_0 - phi_1)/dx - rho_0 dx/(2 eps0), E_N = (phi_N-1 - phi_N)/dx + rho_N dx/(2 eps0).
+ *  C-5  An electrode node owns half a cell of volume.
+ *  C-7  One null-collision trial per particle and step: a candidate if u < P_max =
+ *       1 - exp(-nu_max dt).
+ *  C-8  nu_max is the largest total collision frequency over the cross-section table.
+ *  C-9  Electron elastic scattering: isotropic in the lab frame off a cold atom, with the
+ *       recoil loss of a fraction (2 m_e / M)(1 - cos chi) of the energy.
+ *  C-10 Ionization: the energy above threshold shared equally by the two electrons, both
+ *       isotropic; the new ion drawn from the gas Maxwellian.
+ *  C-11 An ion-induced electron starts at the struck electrode with see_energy_ev, isotropic
+ *       into the gap.
+ *  C-12 Absorbed iff x <= 0 or x >= L; a reflected electron has x mirrored and vx negated and
+ *       is removed if still outside.
+ *  C-13 Ar+ - Ar: isotropic scattering in the centre-of-mass frame, or charge transfer (the ion
+ *       takes the sampled atom's velocity).
+ *  C-14 Deposit in fixed point: 2^32 per superparticle, w_R = rint(f 2^32) (ties to even),
+ *       w_L = 2^32 - w_R.
+ *  C-15 Compaction: removed particles leave holes; births, ranked in particle order and given
+ *       ids next_id + rank, fill the holes in rank order and then follow the last particle;
+ *       survivors beyond the new count fill the holes that remain below it.
+ *  C-16 Random numbers: Philox4x32-10, key (seed, instance), counter (id, step,
+ *       species | purpose | block, 0).
+ *  C-18 EEPF: electrons with |x - L/2| < dx/2, sampled every step.
+ *  C-19 omega_pe and lambda_D from the time-averaged centre density and k T_e = (2/3) <eps>
+ *       of the centre EEPF.
+ *  C-20 N_D = n_e(L/2) A lambda_D / W, superparticles per Debye length.
+ *  C-21 Gamma = W x ions absorbed at an electrode / (A x time), the mean of both electrodes.
+ *  C-22 Initial load: x uniform in (0, L), Maxwellian velocities, ids 0 .. N-1.
+ *  C-23 The tridiagonal Poisson system solved exactly through its discrete Green's function in
+ *       integer arithmetic, each output value rounded once.
+ *  C-XS Closed-form cross sections (Phelps' tables are not available): electron elastic,
+ *       excitation at 11.55 eV, Lotz-type ionization at 15.76 eV; Ar+ - Ar isotropic and
+ *       charge transfer.
  */
 #include <math.h>
 #include <stdint.h>
@@ -60,7 +100,7 @@ typedef struct {
 
 typedef struct {
   orc_params p;
-  /* derived (§2, DESIGN contract 2.1) */
+  /* derived quantities (§2), computed once in this order */
   int nc, nx;
   double dx, inv_dx, inv_2dx, dt, ng, qm_dt[2], emfac_e, spd2_e, mu, emfac_rel, spd2_rel,
       emfac_ilab, mr2, sig_e, sig_i, v_see, efac, rfac, den1, den2, mass[2];
@@ -113,7 +153,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* two uniforms in (0,1) from one block: (2k+1)*2^-53 with k 52 bits (contract 2.2) */
+/* two uniforms in (0,1) from one block: (2k+1)*2^-53 with k 52 bits */
 static double u52(uint32_t hi, uint32_t lo) {
   uint64_t k = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12);
   return (double)(2 * k + 1) * 0x1p-53;
@@ -156,7 +196,7 @@ void orc_uniform_pair(uint64_t seed, uint32_t instance, int species, int purpose
 }
 
 /* --------------------------------------------------------------- natural logarithm
- * Own implementation (contract 2.2): binary-exponent argument reduction to
+ * Own implementation: binary-exponent argument reduction to
  * m in [sqrt(1/2), sqrt(2)) and the series ln m = 2 artanh t, t = (m-1)/(m+1),
  * summed to t^23.  Used only by the polar Gaussian sampler; the input is a positive
  * normal number there. */
@@ -292,7 +332,7 @@ static void build_tables(orc_sim *S) {
   }
 }
 
-/* piecewise-linear interpolant of the cumulative fractions (contract 2.4) */
+/* piecewise-linear interpolant of the cumulative fractions between table nodes */
 static void lookup(const double *F, double eps, double out[3]) {
   double t = eps * XS_INV_DE;
   double kf = floor(t);

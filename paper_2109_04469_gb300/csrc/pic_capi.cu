@@ -83,7 +83,7 @@ Derived derive(const pic_params& p) {
   return d;
 }
 
-// nu_m at the table nodes, nu_max (reading C-8), cumulative fractions [k][4] (contract 2.4)
+// nu_m at the table nodes, nu_max (reading C-8), cumulative fractions [k][4]
 void build_tables(const pic_params& p, Derived& d, std::vector<double>& Fe,
                   std::vector<double>& Fi) {
   std::vector<double> nu((size_t)kXsNodes * 3);
@@ -802,7 +802,7 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   return out->omega_pe_dt_max > 2.0 ? PIC_WARN_UNSTABLE : PIC_OK;
 }
 
-// ------------------------------------------------------------ checkpoint / resume (NEXT-4)
+// ------------------------------------------------------------ checkpoint / resume
 }  // extern "C"
 
 namespace {

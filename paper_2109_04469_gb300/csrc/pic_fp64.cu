@@ -50,7 +50,7 @@ __device__ __forceinline__ void deposit_to(const DevCtx& K, unsigned long long* 
   deposit_at(C, j, f);
 }
 
-// Piecewise-linear interpolant of the cumulative collision fractions (contract 2.4).
+// Piecewise-linear interpolant of the cumulative collision fractions between table nodes.
 __device__ __forceinline__ void lookup(const double* __restrict__ F, double eps, double& f0,
                                        double& f1, double& f2) {
   const double t = eps * kXsInvDe;

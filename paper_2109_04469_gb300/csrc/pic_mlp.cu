@@ -1,4 +1,4 @@
-// pic_mlp.cu -- the surrogate network of the parameter scans: a
+// pic_mlp.cu -- the surrogate network of the parameter scans of §3 (the paper has none): a
 // 7 -> 256 -> 256 -> 192 MLP with GELU, BF16 weights and activations, FP32 accumulation,
 // trained and evaluated by this file's kernels.  Every matrix product runs on the tcgen05
 // tensor cores (pic_tc.cuh): operand tiles brought into shared memory by TMA tensor copies in

@@ -1,5 +1,5 @@
-"""Surrogate of the parameter scans: a 7 -> 256 -> 256 -> 192 network,
-trained on the ensemble's own outputs, that maps a setting (pressure, voltage, time step,
+"""Surrogate of the §3 parameter scans: a 7 -> 256 -> 256 -> 192 network, trained on the
+ensemble's own outputs, that maps a setting (pressure, voltage, time step,
 grid spacing, weight, R, gamma) to the RF-averaged electron density profile (128 points over
 x/L) and the centre EEPF (64 bins), and flags the settings that would break the accuracy
 criteria the paper revisits (§3.5: omega_pe dt <= 0.2, P_coll <= 0.05, dx <= lambda_D).
