@@ -606,12 +606,10 @@ __device__ __forceinline__ void block_pass32(const DevCtx& K, unsigned step, lon
   const int gw = blockIdx.x * kWarps32 + (threadIdx.x >> 5);
   const long long q0 = range_begin(n, gw, GW), q1 = range_begin(n, gw + 1, GW);
   long long hk = q0, ek = q0, ik = q0;  // list slots of this warp
-  // rounds: uniform across the block (the widest warp range of the block decides)
-  long long wmax = 0;
-  for (int w = 0; w < kWarps32; ++w) {
-    const int g = blockIdx.x * kWarps32 + w;
-    wmax = max(wmax, range_begin(n, g + 1, GW) - range_begin(n, g, GW));
-  }
+  // rounds: uniform across the grid; no warp range exceeds ceil(units / GW) units of 32
+  // particles (range_begin floors units g / GW), and an empty round only costs a flush
+  const long long units = (n + kUnit - 1) / kUnit;
+  const long long wmax = (units + GW - 1) / GW * kUnit;
   const int rounds = (int)((wmax + kRoundPerWarp - 1) / kRoundPerWarp);
   bool ok = true;
   for (int r = 0; r < rounds; ++r) {
