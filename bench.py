@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--stress-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--ensemble-members", type=int, default=64)
