@@ -27,6 +27,17 @@ enum : int {
   kCnIIso, kCnICx, kCnECand, kCnICand, kCnEepfN, kCnEepfEsum, kCnDropped
 };
 
+// Exact floor(x / d) for 0 <= x < 2^62 and 1 <= d < 2^32 with no 64-bit division: with
+// m = ceil(2^64 / d) (0 for d = 1), umulhi(x, m) exceeds x / d by less than x / 2^64 < 1, so
+// it is the quotient or one more, and one multiply tells which.
+struct Divider {
+  unsigned long long m;
+  long long d;
+};
+__host__ __device__ __forceinline__ Divider make_divider(long long d) {
+  return Divider{d <= 1 ? 0ull : ~0ull / (unsigned long long)d + 1ull, d};
+}
+
 // Compaction totals of one species for the current step (written by the last particle
 // block, read by the placement launch).
 struct CompactTot {
@@ -50,6 +61,20 @@ __host__ __device__ __forceinline__ long long range_begin(long long n, int b, in
   const long long p = u * kUnit;
   return p < n ? p : n;
 }
+#ifdef __CUDACC__
+__device__ __forceinline__ long long div_floor(long long x, const Divider& v) {
+  if (v.m == 0ull) return x;
+  long long q = (long long)__umul64hi((unsigned long long)x, v.m);
+  if (q * v.d > x) --q;
+  return q;
+}
+// range_begin(n, b, G) with dG = make_divider(G)
+__device__ __forceinline__ long long range_begin_d(long long n, int b, const Divider& dG) {
+  const long long units = (n + kUnit - 1) / kUnit;
+  const long long p = div_floor(units * (long long)b, dG) * kUnit;
+  return p < n ? p : n;
+}
+#endif
 // The block whose range holds particle index t (0 <= t < n).
 __host__ __device__ __forceinline__ int range_owner(long long n, long long t, int G) {
   const long long units = (n + kUnit - 1) / kUnit;
@@ -138,6 +163,7 @@ struct DevCtx {
   // start at the slot of its first particle and are in particle order.  The counts are per
   // owner ([nlist] entries); the placement launch forms their prefixes in shared memory.
   int nlist;            // list owners of the particle pass
+  Divider gw_div;       // divider of the FP32 particle grid's warp count
   int nfield;           // field blocks of the placement launch
   int *hole_idx[2];     // [cap]: hole indices
   int *hole_cnt[2];

@@ -604,7 +604,7 @@ __device__ __forceinline__ void block_pass32(const DevCtx& K, unsigned step, lon
                                              long long (*wb)[kWarps32]) {
   const int GW = gridDim.x * kWarps32;  // warps of the grid
   const int gw = blockIdx.x * kWarps32 + (threadIdx.x >> 5);
-  const long long q0 = range_begin(n, gw, GW), q1 = range_begin(n, gw + 1, GW);
+  const long long q0 = range_begin_d(n, gw, K.gw_div), q1 = range_begin_d(n, gw + 1, K.gw_div);
   long long hk = q0, ek = q0, ik = q0;  // list slots of this warp
   // rounds: uniform across the grid; no warp range exceeds ceil(units / GW) units of 32
   // particles (range_begin floors units g / GW), and an empty round only costs a flush
@@ -1009,6 +1009,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
   __shared__ unsigned sStep[kMaxEnsemble];
   __shared__ int sG[kMaxEnsemble], sC0[kMaxEnsemble + 1], sOrd[kMaxEnsemble];
   __shared__ int sUpw[kMaxEnsemble];  // owners per warp per chunk
+  __shared__ Divider sGd[kMaxEnsemble];  // dividers of the owner counts
   __shared__ unsigned sChunk;
   __shared__ unsigned long long sCnt[kNumCounters];
   __shared__ CompactTot sT[2];
@@ -1026,6 +1027,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
     sNi[s] = ni;
     sStep[s] = step;
     sG[s] = active ? (int)g : 0;
+    sGd[s] = make_divider(g);
     // owners per warp between counter flushes: every owner holds at most
     // ceil(N / G) + 64 particles (32-particle rounding per species); keep the warp's sum
     // within kMaxEnsUnit so the 32-bit shared counters stay in range
@@ -1106,11 +1108,12 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
       const long long g = (long long)(c - (unsigned)sC0[k]) * kWarps32 * upw + u * kWarps32 + warp;
       if (g < G) {
         // after a timed-out wait (status set) the warp's remaining owners list nothing
-        const long long q0 = range_begin(ne, (int)g, G), q1 = range_begin(ne, (int)g + 1, G);
+        const Divider& dG = sGd[s];
+        const long long q0 = range_begin_d(ne, (int)g, dG), q1 = range_begin_d(ne, (int)g + 1, dG);
         long long hk = q0, ek = q0, ik = q0;
         if (ok) ok = warp_pass32<0>(K, step, q0, q1, sE, sC, sC + nx, sCnt, P, Q, hk, ek, ik);
         const int he = (int)(hk - q0), be0 = (int)(ek - q0), bi = (int)(ik - q0);
-        const long long r0 = range_begin(ni, (int)g, G), r1 = range_begin(ni, (int)g + 1, G);
+        const long long r0 = range_begin_d(ni, (int)g, dG), r1 = range_begin_d(ni, (int)g + 1, dG);
         hk = ek = ik = r0;
         if (ok) ok = warp_pass32<1>(K, step, r0, r1, sE + nx, sC, sC + nx, sCnt, P, Q, hk, ek, ik);
         const int hi_ = (int)(hk - r0), be1 = (int)(ek - r0);
