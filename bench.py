@@ -199,7 +199,8 @@ def run_reference(args, cfg):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "particles_per_species": c["init_per_species"],
-                       "n_cells": c["n_cells"], "precision": "fp64"},
+                       "n_cells": c["n_cells"], "steps_per_rf": c["steps_per_rf"],
+                       "precision": "fp64 (the oracle)", "parallelism": "one host thread"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
