@@ -171,6 +171,47 @@ def cpu_baseline(cfg: dict, steps: int) -> dict:
                       f"steps after 2 warm-up steps, plain C FP64, 1 thread, {dt:.1f} s"}
 
 
+def ensemble_cpu_baseline(members: int, budget_s: float = 10.0) -> dict:
+    """The oracle on the batched scan: one member per host core, all cores stepping their
+    member concurrently (the C oracle releases the interpreter lock), for about budget_s of
+    wall time; the aggregate particle-steps/s over all threads.  The members are spread over
+    the scan (every members/cores-th one), so the sample mixes its sizes and pressures."""
+    import os
+    import threading
+
+    from oracle import oracle as O
+    from paper_2109_04469_gb300 import workloads
+
+    scan = workloads.ensemble_members(members)
+    cores = max(1, min(os.cpu_count() or 1, len(scan)))
+    pick = [scan[(i * len(scan)) // cores][0] for i in range(cores)]
+    done = [0] * cores
+    start = threading.Barrier(cores + 1)
+
+    def run(i: int, t_end: list):
+        sim = O.OracleSim(dict(pick[i]))  # loaded in this thread, outside the window
+        sim.step(1)  # warm-up step
+        start.wait()
+        while time.perf_counter() < t_end[0]:
+            done[i] += sim.count(0) + sim.count(1)
+            sim.step(1)
+
+    t_end = [float("inf")]
+    threads = [threading.Thread(target=run, args=(i, t_end)) for i in range(cores)]
+    for th in threads:
+        th.start()
+    start.wait()
+    t0 = time.perf_counter()
+    t_end[0] = t0 + budget_s
+    for th in threads:
+        th.join()
+    wall = time.perf_counter() - t0
+    return {"value": sum(done) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} of the {len(scan)} scan members (every {len(scan) // cores}-th), "
+                      f"one per host thread, stepped concurrently for {wall:.1f} s after one "
+                      f"warm-up step each; plain C FP64"}
+
+
 def run_reference(args, cfg):
     rank, _, world = dist_env()
     if rank != 0:
@@ -543,6 +584,8 @@ def main():
                            "births (counted), which is what a status of -3 reports"}
         if "fp64" in runs and "fp64" != head_prec:
             line["ensemble"]["speedup_vs_fp64_plain"] = ev / line["fp64_plain"]["value"]
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            line["ensemble"]["cpu_baseline"] = ensemble_cpu_baseline(args.ensemble_members)
     if not args.no_stress:
         line["stress"] = measure_stress(args, torch, dist, local_rank, rank, peak)
     if not args.no_surrogate and rank == 0:

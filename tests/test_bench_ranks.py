@@ -63,3 +63,13 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args(), {}) is None
     assert capsys.readouterr().out == ""
+
+
+def test_ensemble_cpu_baseline_uses_every_thread():
+    """The scan's oracle baseline steps one member per host thread concurrently and reports
+    the aggregate rate with the thread count."""
+    import bench
+
+    r = bench.ensemble_cpu_baseline(4, budget_s=0.5)
+    assert r["kind"] == "oracle" and r["unit"] == "particle-steps/s"
+    assert 1 <= r["cores"] <= 4 and r["value"] > 0
