@@ -153,12 +153,12 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(cfg: dict, steps: int) -> dict:
+def cpu_baseline(cfg: dict, steps: int, warmup: int = 2) -> dict:
     """The FP64 oracle as it stands, one thread, on the full workload for a bounded window."""
     from oracle import oracle as O
 
     sim = O.OracleSim(cfg)
-    sim.step(2)
+    sim.step(warmup)
     n0 = sim.count(0) + sim.count(1)
     t = time.perf_counter()
     parts = 0
@@ -168,7 +168,7 @@ def cpu_baseline(cfg: dict, steps: int) -> dict:
     dt = time.perf_counter() - t
     return {"value": parts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{cfg.get('name', '')} full population ({n0} superparticles), {steps} "
-                      f"steps after 2 warm-up steps, plain C FP64, 1 thread, {dt:.1f} s"}
+                      f"steps after {warmup} warm-up steps, plain C FP64, 1 thread, {dt:.1f} s"}
 
 
 def ensemble_cpu_baseline(members: int, budget_s: float = 10.0) -> dict:
@@ -407,7 +407,8 @@ def measure_ensemble(args, torch, dist, rank: int) -> dict:
     return out
 
 
-def measure_stress(args, torch, dist, local_rank: int, rank: int, peak: float) -> dict:
+def measure_stress(args, torch, dist, local_rank: int, rank: int, peak: float,
+                   world: int = 1) -> dict:
     """The stress workload (5e7 + 5e7 superparticles, 1025 nodes): both precisions, the split
     of a step between the particle launch, the placement launch and the field solve, and the
     field solve's share of the step."""
@@ -433,6 +434,8 @@ def measure_stress(args, torch, dist, local_rank: int, rank: int, peak: float) -
                      "roofline_frac_hbm": r["alg_bytes_per_launch"] / (r["push_ms"] / 1e3)
                      / 1e9 / peak,
                      "status": r["status"], "clocks": r["clocks"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(dict(scfg, name=name), 2, warmup=1)
     return out
 
 
@@ -587,7 +590,7 @@ def main():
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             line["ensemble"]["cpu_baseline"] = ensemble_cpu_baseline(args.ensemble_members)
     if not args.no_stress:
-        line["stress"] = measure_stress(args, torch, dist, local_rank, rank, peak)
+        line["stress"] = measure_stress(args, torch, dist, local_rank, rank, peak, world)
     if not args.no_surrogate and rank == 0:
         line["surrogate"] = measure_surrogate(torch)
     if "e2e" in head:
