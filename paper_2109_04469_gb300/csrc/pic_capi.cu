@@ -84,8 +84,7 @@ Derived derive(const pic_params& p) {
 }
 
 // nu_m at the table nodes, nu_max (reading C-8), cumulative fractions [k][4]
-void build_tables(const pic_params& p, Derived& d, std::vector<double>& Fe,
-                  std::vector<double>& Fi) {
+void build_tables(Derived& d, std::vector<double>& Fe, std::vector<double>& Fi) {
   std::vector<double> nu((size_t)kXsNodes * 3);
   for (int s = 0; s < 2; ++s) {
     double numax = 0.0;
@@ -319,7 +318,7 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   Derived& d = h->d;
   d = derive(*p);
   std::vector<double> Fe, Fi;
-  build_tables(*p, d, Fe, Fi);
+  build_tables(d, Fe, Fi);
   const int nc = p->n_cells, nx = nc + 1;
   std::vector<double> inv_den((size_t)nx, 0.0);
   double den = 2.0;
