@@ -3,7 +3,6 @@ flux, §3.5 criteria) and whole-loop invariants of the cycle of §2."""
 import math
 
 import numpy as np
-from scipy import stats
 
 from oracle import oracle as O
 from paper_2109_04469_gb300 import workloads

@@ -5,7 +5,6 @@ from fractions import Fraction
 
 import numpy as np
 import pytest
-from scipy import stats
 
 from oracle import oracle as O
 
