@@ -8,7 +8,9 @@ The FP32 path is not bit-identical to the oracle; its bar is:
   * RF-averaged densities, the centre EEPF mean energy and the ion flux agree with the
     oracle within 3 combined standard errors over independent seeds, and so do the density
     profile (8 segments) and the EEPF (5 energy bands), bin by bin (|z| < 4, sum of z^2
-    below the 99.9 % point of chi^2(13)).
+    below the 99.9 % point of chi^2(13));
+  * at the production size, one RF period of FP32 agrees with the FP64 path (the oracle's
+    step bit for bit) within 1-2 % in counts, profile, ion flux and centre T_e.
 """
 import math
 
@@ -176,6 +178,34 @@ def test_fp32_full_size_workload_runs():
     assert int(g["Ce"].sum()) == ne * 2**32 and int(g["Ci"].sum()) == ni * 2**32
     assert 1.9e6 < ne < 2.1e6 and 1.9e6 < ni < 2.1e6
     sim.close()
+
+
+def test_fp32_production_rf_period_matches_fp64():
+    """The production workload (2e6 + 2e6 superparticles, 400 cells) over one RF period (3000
+    steps) from the same load in both precisions: the FP64 GPU path is the oracle's step bit
+    for bit, so this compares FP32 with the oracle at full size.  Measured on GB300: counts
+    +0.04 %, the time-averaged density in 8 segments within 0.4 %, ion flux -0.05 %, centre
+    T_e +0.15 %; the bounds are about five times those (the runs decorrelate, so the
+    differences are sampling noise of 2.5e6 particles)."""
+    out = {}
+    for prec in (pic.PIC_FP64, pic.PIC_FP32):
+        cfg = workloads.params("ccp_1pa_300v_400c", capacity_per_species=8_000_000)
+        cfg["precision"] = prec
+        sim = pic.Simulation(cfg)
+        sim.step(3000)
+        assert sim.sync() == 0
+        d = sim.diag()
+        nodes = np.array_split(np.arange(cfg["n_cells"] + 1), 8)
+        out[prec] = dict(n=sim.counts(), seg=[float(np.mean(d["n_e"][i])) for i in nodes],
+                         flux=d["ion_flux"], te=d["te_center_ev"])
+        sim.close()
+    a, b = out[pic.PIC_FP32], out[pic.PIC_FP64]
+    rel = lambda x, y: abs(x - y) / abs(y)
+    for s in (0, 1):
+        assert rel(a["n"][s], b["n"][s]) < 0.01, (s, a["n"], b["n"])
+    for k, (x, y) in enumerate(zip(a["seg"], b["seg"])):
+        assert rel(x, y) < 0.02, (k, x, y)
+    assert rel(a["flux"], b["flux"]) < 0.02 and rel(a["te"], b["te"]) < 0.02
 
 
 def test_fp32_stress_workload_runs():
