@@ -280,16 +280,22 @@ class OracleSim:
 
     def diag(self) -> dict:
         """Physical diagnostics from the raw accumulators (§3.1, §3.4, §3.5; C-18..C-21)."""
+        pe = self.particles(0)
         return derived_diagnostics(self.cfg, self.accum(), self.derived(),
-                                   self.count(0), self.count(1), self.particles(0)["vx"])
+                                   self.count(0), self.count(1), pe["vx"], pe["vy"], pe["vz"])
 
 
 # physical constants (CODATA 2018) used by the derived diagnostics
 _QE, _ME, _EPS0 = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
+# floor of the runaway-energy threshold (eV) of the instability flag, for undriven runs
+RUNAWAY_FLOOR_EV = 100.0
 
 
-def derived_diagnostics(cfg, acc, der, n_e, n_i, vx_e) -> dict:
-    """Densities, EEPF, FEDFs, ion flux and the stability/accuracy criteria of §3.5."""
+def derived_diagnostics(cfg, acc, der, n_e, n_i, vx_e, vy_e=None, vz_e=None) -> dict:
+    """Densities, EEPF, FEDFs, ion flux and the stability/accuracy criteria of §3.5, and the
+    instability flag: ω_pe Δt above the leapfrog bound 2 (§3.5), or a runaway in which the
+    electrons' mean kinetic energy exceeds the largest energy the drive can give them,
+    e |V_rf| (at least RUNAWAY_FLOOR_EV)."""
     nc = cfg["n_cells"]
     steps = acc["steps"]
     W, A, dx, dt = cfg["weight"], cfg["area_m2"], der["dx"], der["dt"]
@@ -340,4 +346,12 @@ def derived_diagnostics(cfg, acc, der, n_e, n_i, vx_e) -> dict:
     out["dx_over_lambda_d"] = dx / lam
     out["n_debye"] = n_c * A * lam / W if np.isfinite(lam) else float("inf")  # C-20
     out["cfl_max"] = (np.abs(vx_e).max() * dt / dx) if len(vx_e) else 0.0
+    if vy_e is not None and len(vx_e):
+        v2 = np.asarray(vx_e) ** 2 + np.asarray(vy_e) ** 2 + np.asarray(vz_e) ** 2
+        out["mean_energy_e_ev"] = float(np.mean(v2)) * (0.5 * _ME / _QE)
+    else:
+        out["mean_energy_e_ev"] = 0.0
+    runaway = max(abs(cfg["v_rf_amp_v"]), RUNAWAY_FLOOR_EV)
+    out["unstable"] = bool(out["omega_pe_dt_max"] > 2.0 or
+                           not (out["mean_energy_e_ev"] <= runaway))
     return out

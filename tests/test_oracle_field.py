@@ -1,5 +1,6 @@
-"""Pins of the oracle's field solve (§2 step 2: Dirichlet Poisson by the Thomas algorithm,
-E by differencing; readings C-4, C-5)."""
+"""Pins of the oracle's field solve (§2 step 2: the Dirichlet finite-difference Poisson system,
+solved exactly through its discrete Green's function (reading C-23) and kept beside the
+Thomas algorithm the paper names; E by differencing; readings C-4, C-5)."""
 import numpy as np
 import pytest
 
@@ -57,7 +58,7 @@ def _random_counts(nc, seed):
 
 @pytest.mark.parametrize("nc", [5, 128, 1024])
 def test_random_charge_against_dense_solve(nc):
-    """The Thomas result equals a dense LU solve (numpy) of the same finite-difference system."""
+    """The field solve equals a dense LU solve (numpy) of the same finite-difference system."""
     L, V, W, A = 0.025, -80.0, 1e5, 1e-4
     s = _sim(n_cells=nc, v_rf_amp_v=V, weight=W)
     Ce, Ci = _random_counts(nc, nc)

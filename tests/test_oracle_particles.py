@@ -106,9 +106,10 @@ def test_uniform_field_leapfrog_exact_parabola():
         assert np.max(np.abs(s.particles(1)["x"] - want)) <= 1e-12 * L, n
 
 
-def _cold_plasma_run(wdt, steps, nc=64, n_per=64 * 64):
+def _cold_plasma_run(wdt, steps, nc=64, n_per=64 * 64, with_sim=False):
     """Electrons on a uniform ion background, displaced by xi = delta sin(2 pi x / L);
-    grounded electrodes.  Returns the electrons' mean displacement projection per step."""
+    grounded electrodes.  Returns the electrons' mean displacement projection per step (and
+    the simulation itself with with_sim)."""
     L = 0.01
     f = 13.56e6
     n0 = 1e15
@@ -136,6 +137,8 @@ def _cold_plasma_run(wdt, steps, nc=64, n_per=64 * 64):
         xi = p["x"][order] - x_eq
         proj.append(float(np.dot(xi, basis)))
     del Nt
+    if with_sim:
+        return np.array(proj), wpe, dt, s
     return np.array(proj), wpe, dt
 
 
@@ -154,6 +157,24 @@ def test_cold_plasma_oscillation_leapfrog_frequency(wdt):
     w_theory = 2 * math.asin(wdt / 2) / dt
     assert abs(w_meas / w_theory - 1) < 0.01, (w_meas / wpe, w_theory / wpe)
     assert np.max(np.abs(y)) < 3 * np.max(np.abs(y[: int(2 * math.pi / wdt) + 2]))
+
+
+@pytest.mark.parametrize("wdt", [0.3, 1.2])
+def test_reported_omega_pe_dt_matches_the_measured_oscillation(wdt):
+    """The criterion ω_pe Δt that the diagnostics report (§3.5, reading C-19: from the
+    time-averaged density at L/2) against the plasma frequency the simulation itself
+    oscillates at: a measured numerical frequency Ω gives ω_pe Δt = 2 sin(Ω Δt / 2) (the
+    leapfrog dispersion relation inverted).  A wrong constant, density scale or centre
+    interpolation in the diagnostic would miss the measured value."""
+    steps = int(10 * 2 * math.pi / wdt)
+    y, _, dt, s = _cold_plasma_run(wdt, steps, with_sim=True)
+    assert len(y) == steps
+    zc = np.where(np.sign(y[:-1]) != np.sign(y[1:]))[0]
+    t = zc + y[zc] / (y[zc] - y[zc + 1])
+    omega = math.pi / (np.mean(np.diff(t)) * dt)
+    measured = 2 * math.sin(omega * dt / 2)
+    d = s.diag()
+    assert abs(d["omega_pe_dt"] / measured - 1) < 0.005, (d["omega_pe_dt"], measured)
 
 
 def test_cold_plasma_unstable_beyond_two():
