@@ -11,6 +11,11 @@ dt = T_RF/3000, 2e6 superparticles per species, R = 0.2, gamma = 0.1.
 Prints one JSON line (rank 0).  Under torchrun each rank runs an independent replica
 (instance = rank): weak scaling, no data-path collective.  ``--impl reference`` times the FP64
 CPU oracle (the checker, plain C, one thread) on the same workload and metric.
+
+  python bench.py --profile-case fp32|fp64|ens|mlp
+
+runs one small, self-contained case of a kernel family (a few launches) and exits: the
+command lines that the ncu summaries under profiles/ were taken with.
 """
 from __future__ import annotations
 
@@ -55,6 +60,11 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--ensemble-members", type=int, default=64)
+    ap.add_argument("--ensemble-steps", type=int, default=20,
+                    help="timed ensemble steps (members grow from their uniform load; the "
+                         "capacity of workloads.ensemble_members holds about 45 steps)")
+    ap.add_argument("--ensemble-warmup", type=int, default=3)
+    ap.add_argument("--profile-case", choices=("fp32", "fp64", "ens", "mlp"), default=None)
     ap.add_argument("--precisions", default="fp32,fp64",
                     help="comma list; the first is the headline, the others are reported beside it")
     return ap.parse_args()
@@ -212,6 +222,17 @@ def ensemble_cpu_baseline(members: int, budget_s: float = 10.0) -> dict:
                       f"warm-up step each; plain C FP64"}
 
 
+def arm_config(args, cfg: dict, world: int) -> dict:
+    """The workload keys of the JSON line, the same for this implementation and the reference
+    arm (the oracle): what is simulated, not how."""
+    return {"workload": args.workload, "particles_per_species": cfg["init_per_species"],
+            "n_cells": cfg["n_cells"], "steps_per_rf": cfg["steps_per_rf"],
+            "pressure_pa": cfg["pressure_pa"], "v_rf_amp_v": cfg["v_rf_amp_v"],
+            "parallelism": f"replicas x{world}",
+            "initial_state": "uniform Maxwellian load (reading C-22), not a converged discharge",
+            "l2": "flushed between timed steps: 256 MiB written, then 256 MiB read"}
+
+
 def run_reference(args, cfg):
     rank, _, world = dist_env()
     if rank != 0:
@@ -233,15 +254,16 @@ def run_reference(args, cfg):
         sim.step(1)
     el = time.perf_counter() - t
     v = parts / el
-    sample = (f"{args.workload}: {c['init_per_species']} initial superparticles per species, "
-              f"{args.warmup} warm-up + {args.steps} timed steps, plain C FP64, 1 thread")
+    sample = (f"{args.workload}: {c['init_per_species']} initial superparticles per species "
+              f"(the workload's {cfg['init_per_species']} scaled to the time budget)"
+              if scale < 1.0 else f"{args.workload}: the full population")
+    sample += (f", {args.warmup} warm-up + {args.steps} timed steps, plain C FP64 oracle, "
+               f"1 host thread (rank 0 only)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "particles_per_species": c["init_per_species"],
-                       "n_cells": c["n_cells"], "steps_per_rf": c["steps_per_rf"],
-                       "precision": "fp64 (the oracle)", "parallelism": "one host thread"},
+            "config": arm_config(args, cfg, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -252,10 +274,21 @@ BYTES_PER_PARTICLE = {  # algorithmic bytes of the particle pass per particle-st
     # FP64: x, vx read and written (32 B) + id read (4 B); a candidate also reads and writes
     # vy, vz (32 B); a removed or born particle moves one 36 B record
     "fp64": (36.0, 32.0, 36.0),
-    # FP32: (offset, vx) read and written (16 B) + cell|countdown u32 read and written (8 B)
-    # + id read (4 B); candidates r/w vy, vz (16 B); a moved record is 24 B
-    "fp32": (28.0, 16.0, 24.0),
+    # FP32 cell + offset: (offset, vx) read and written (16 B) + the cell read and written
+    # (4 B) + id read (4 B) = 24 B; candidates r/w vy, vz (16 B); a moved record is 24 B
+    "fp32": (24.0, 16.0, 24.0),
 }
+# the FP32 layout's own bytes: the null-collision countdown shares a u32 with the cell, so the
+# cell word is 4 B each way (28 B per particle-step)
+FP32_LAYOUT_BYTES = 28.0
+
+
+def alg_bytes(precision: str, parts: int, dc, per=None) -> float:
+    """Algorithmic bytes of the particle passes of a run: `parts` particle-steps, the collision
+    candidates and the records moved (removed + born) from the counter deltas dc."""
+    p0, cand, rec = BYTES_PER_PARTICLE[precision]
+    turnover = int(dc[0] + dc[1] + dc[2] + dc[3] + 2 * dc[8] + dc[5])
+    return (p0 if per is None else per) * parts + cand * float(dc[11] + dc[12]) + rec * turnover
 
 
 class L2Flush:
@@ -334,12 +367,15 @@ def measure(pcfg: dict, precision: str, args, torch, dist, local_rank: int,
             ev1.synchronize()
             field_ms += ev0.elapsed_time(ev1) / 10
     status = sim.status()
-    per, cand, rec = BYTES_PER_PARTICLE[precision]
-    turnover = int(dc[0] + dc[1] + dc[2] + dc[3] + 2 * dc[8] + dc[5])
-    alg_bytes = per * parts + cand * float(dc[11] + dc[12]) + rec * turnover
+    ab = alg_bytes(precision, parts, dc)
+    ab_layout = alg_bytes(precision, parts, dc, FP32_LAYOUT_BYTES) if precision == "fp32" else ab
+    per_step = sorted(float(a.elapsed_time(b)) for a, b in evs)
     out = dict(step_ms=step_ms, parts=parts, push_ms=ms2[0] / args.steps,
                place_ms=ms2[1] / args.steps, field_ms=field_ms,
-               alg_bytes_per_launch=alg_bytes / args.steps, clocks=clocks, status=status)
+               alg_bytes_per_launch=ab / args.steps,
+               layout_bytes_per_launch=ab_layout / args.steps, clocks=clocks, status=status,
+               step_ms_quantiles=[per_step[len(per_step) // 10], statistics.median(per_step),
+                                  per_step[(9 * len(per_step)) // 10]])
     if with_e2e:
         out["e2e"] = run_e2e(sim, args, torch)
     sim.close()
@@ -361,24 +397,25 @@ def measure_ensemble(args, torch, dist, rank: int) -> dict:
             c = dict(c, precision=pic.PIC_FP32, instance=c["instance"] + 1000 * rank)
             sims.append(pic.Simulation(c))
         ens = pic.Ensemble(sims, [t for _, t in members])
-        chosen = ens.autotune(3)
-        ens.step(args.warmup)
+        chosen = ens.autotune(2)
+        ens.step(args.ensemble_warmup)
     try:
         ens.sync()
     except pic.PicError:
         pass  # a sticky member status is reported after the timed steps
     c0 = sum(s.accum()["counters"].astype(np.int64) for s in sims)
     n = len(sims)
-    counts = torch.zeros((args.steps + 1, n, 2), dtype=torch.int64, pin_memory=True)
+    steps = args.ensemble_steps
+    counts = torch.zeros((steps + 1, n, 2), dtype=torch.int64, pin_memory=True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for i, sim in enumerate(sims):
             sim.counts_async(counts[0, i])
-        for k in range(args.steps):
+        for k in range(steps):
             evs[k][0].record(stream)
             ens.step(1)
             evs[k][1].record(stream)
@@ -392,13 +429,13 @@ def measure_ensemble(args, torch, dist, rank: int) -> dict:
     except pic.PicError as e:  # reported in the line (e.g. births dropped at capacity)
         status = e.code
     step_ms = float(sum(a.elapsed_time(b) for a, b in evs))
-    parts = int(counts[:args.steps].sum().item())
+    parts = int(counts[:steps].sum().item())
     dc = sum(s.accum()["counters"].astype(np.int64) for s in sims) - c0
-    per, cand, rec = BYTES_PER_PARTICLE["fp32"]
-    turnover = int(dc[0] + dc[1] + dc[2] + dc[3] + 2 * dc[8] + dc[5])
-    alg_bytes = per * parts + cand * float(dc[11] + dc[12]) + rec * turnover
     info = ens.info()
-    out = dict(step_ms=step_ms, parts=parts, alg_bytes=alg_bytes, status=status,
+    grow = counts[steps].double() / counts[0].double().clamp(min=1)
+    out = dict(step_ms=step_ms, parts=parts, alg_bytes=alg_bytes("fp32", parts, dc),
+               layout_bytes=alg_bytes("fp32", parts, dc, FP32_LAYOUT_BYTES), status=status,
+               steps=steps, max_growth=float(grow.max().item()),
                members=n, particles=int(counts[0].sum().item()),
                schedule={"unit": chosen[0], "blocks_per_sm": chosen[1], "grid": info["grid"],
                          "graph": bool(info["graph"])})
@@ -433,7 +470,11 @@ def measure_stress(args, torch, dist, local_rank: int, rank: int, peak: float,
                      "field_alone_ms": r["field_ms"], "poisson_share": r["field_ms"] / ms,
                      "roofline_frac_hbm": r["alg_bytes_per_launch"] / (r["push_ms"] / 1e3)
                      / 1e9 / peak,
+                     "bytes_per_particle_step": BYTES_PER_PARTICLE[prec][0],
                      "status": r["status"], "clocks": r["clocks"]}
+        if prec == "fp32":
+            out[prec]["roofline_frac_hbm_layout_28b"] = (
+                r["layout_bytes_per_launch"] / (r["push_ms"] / 1e3) / 1e9 / peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(dict(scfg, name=name), 2, warmup=1)
     return out
@@ -500,8 +541,43 @@ def reduce_ranks(torch, dist, step_ms: float, parts: int, device: str = "cuda"):
     return float(t.item()), int(p.item())
 
 
+def profile_case(mode: str) -> None:
+    """Small, self-contained launches of one kernel family for ncu: the FP32 or FP64 particle
+    pass on the production workload (5 steps), a 16-member ensemble (5 steps) and the
+    surrogate network's training GEMMs (3 Adam steps at batch 1024)."""
+    import torch
+
+    from paper_2109_04469_gb300 import pic, workloads
+
+    if mode in ("fp32", "fp64"):
+        prec = pic.PIC_FP32 if mode == "fp32" else pic.PIC_FP64
+        sim = pic.Simulation(workloads.params("ccp_1pa_300v_400c", precision=prec))
+        sim.step(5)
+        print("status", sim.sync())
+    elif mode == "ens":  # 16 scan members (2.5e5-1e6 superparticles each)
+        members = workloads.ensemble_members(16, per_run=(2.5e5, 1.0e6))
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            sims = [pic.Simulation(dict(c, precision=pic.PIC_FP32)) for c, _ in members]
+            ens = pic.Ensemble(sims, [10**9] * len(sims))
+            ens.configure(2048, 2, True)
+            ens.step(5)
+        print("status", ens.sync())
+    else:  # mlp
+        net = pic.Mlp(1024, seed=1)
+        x = torch.randn(1024, 7, device="cuda")
+        t = torch.randn(1024, 192, device="cuda")
+        for _ in range(3):
+            net.train_step(x, t, 1e-3, want_loss=False)
+        torch.cuda.synchronize()
+        print("ok")
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     from paper_2109_04469_gb300 import workloads
 
     cfg = workloads.params(args.workload)
@@ -531,23 +607,29 @@ def main():
     value = total_parts / (total_ms / 1e3)
     peak, peak_src = measured_peak()
     achieved = head["alg_bytes_per_launch"] / (head["push_ms"] / 1e3) / 1e9
+    achieved_layout = head["layout_bytes_per_launch"] / (head["push_ms"] / 1e3) / 1e9
     kname = "k_push_fp32" if head_prec == "fp32" else "k_push_fp64"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
             "traffic": profiled_traffic(f"push_{head_prec}", args.workload),
             "kernel": kname, "alg_bytes_per_launch": head["alg_bytes_per_launch"],
+            "bytes_per_particle_step": BYTES_PER_PARTICLE[head_prec][0],
             "launch_ms": head["push_ms"]}
+    if head_prec == "fp32":
+        roof["frac_layout_28b"] = achieved_layout / peak
     ms_step = total_ms / args.steps
+    q = head["step_ms_quantiles"]
+    parts_per_step = total_parts / args.steps
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if head_prec == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "particles_per_species": cfg["init_per_species"],
-                       "n_cells": cfg["n_cells"], "steps_per_rf": cfg["steps_per_rf"],
-                       "precision": head_prec + (" particles, fp64 field" if head_prec == "fp32"
-                                                 else ""),
-                       "parallelism": f"replicas x{world}",
-                       "l2": "flushed between timed steps: 256 MiB written, then 256 MiB read"},
+            "config": arm_config(args, cfg, world),
+            "per_step_spread": {"value_p10": parts_per_step / world / (q[2] / 1e3),
+                                "value_median": parts_per_step / world / (q[1] / 1e3),
+                                "value_p90": parts_per_step / world / (q[0] / 1e3),
+                                "note": "rank-0 per-step event times (10 %, 50 %, 90 % "
+                                        "quantiles of the rate)"},
             "roofline": roof,
             "kernel_ms_per_step": {"particles": head["push_ms"],
                                    "placement_and_next_field": head["place_ms"],
@@ -555,6 +637,7 @@ def main():
             "poisson_share": head["field_ms"] / ms_step,
             "compaction_share": max(0.0, head["place_ms"] - head["field_ms"]) / ms_step,
             "gpu_launches": 2 * args.steps,
+            "precision": head_prec + (" particles, fp64 field" if head_prec == "fp32" else ""),
             "clocks": head["clocks"], "status": head["status"]}
     for prec, r in runs.items():
         if prec == head_prec:
@@ -570,22 +653,28 @@ def main():
         et, ep = reduce_ranks(torch, dist, er["step_ms"], er["parts"])
         ev = ep / (et / 1e3)
         eb = er["alg_bytes"] / (er["step_ms"] / 1e3) / 1e9  # the launch is the whole step
+        ebl = er["layout_bytes"] / (er["step_ms"] / 1e3) / 1e9
+        ok = er["status"] == 0
         line["ensemble"] = {
-            "value": ev, "unit": UNIT, "ms_per_step": et / args.steps,
+            # a run that dropped births no longer follows §2 step 6: no value is reported
+            "value": ev if ok else None, "unit": UNIT,
+            "ms_per_step": et / er["steps"], "steps": er["steps"],
+            "warmup": args.ensemble_warmup,
             "members": er["members"], "particles_per_step": er["particles"],
+            "max_population_growth": er["max_growth"],
             "workload": "64 uneven ccp scans (workloads.ensemble_members): p 1-20 Pa, "
                         "V 100-500 V, N_t 500-4000, 100-800 cells, 2.5e5-4e6 superparticles per "
-                        "run, R 0-0.7, gamma 0-0.4",
+                        "run, R 0-0.7, gamma 0-0.4; uniform Maxwellian loads",
             "l2": "state of many GB, larger than L2: steps back to back",
             "schedule": er["schedule"],
             "roofline": {"bound": "hbm", "achieved": eb, "peak": peak, "unit": "GB/s",
-                         "frac": eb / peak, "kernel": "k_ensemble_step"},
-            "status": er["status"],
-            "status_note": "members start from a uniform Maxwellian, far from their steady "
-                           "state; settings that ionize fastest outgrow their capacity "
-                           "(3x the initial population) within the run and drop the excess "
-                           "births (counted), which is what a status of -3 reports"}
-        if "fp64" in runs and "fp64" != head_prec:
+                         "frac": eb / peak, "frac_layout_28b": ebl / peak,
+                         "kernel": "k_ensemble_step"},
+            "status": er["status"]}
+        if not ok:
+            line["ensemble"]["refused"] = ("non-zero status: a member dropped births or a wait "
+                                          "timed out, so the run is not the method's")
+        if ok and "fp64" in runs and "fp64" != head_prec:
             line["ensemble"]["speedup_vs_fp64_plain"] = ev / line["fp64_plain"]["value"]
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             line["ensemble"]["cpu_baseline"] = ensemble_cpu_baseline(args.ensemble_members)

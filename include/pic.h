@@ -72,7 +72,11 @@ extern "C" {
 #define PIC_ERR_WORKSPACE (-5)  /* workspace missing, too small or misaligned */
 #define PIC_ERR_TIMEOUT (-6)    /* a bounded device wait ran out; results of the step invalid */
 #define PIC_ERR_SCRATCH (-7)    /* n_cells above PIC_FIELD_STATIC_MAX_CELLS (pic_field_solve_static) */
-#define PIC_WARN_UNSTABLE 1     /* omega_pe*dt > 2: the leapfrog stability bound of §3.5 */
+#define PIC_WARN_UNSTABLE 1     /* a numerically unstable run (§3.5): omega_pe*dt above the
+                                   leapfrog stability bound 2, or a runaway electron energy:
+                                   the mean kinetic energy of the electrons above
+                                   max(e |V_rf|, PIC_RUNAWAY_FLOOR_EV) */
+#define PIC_RUNAWAY_FLOOR_EV 100.0
 
 #define PIC_FP64 0 /* FP64 particle state; bit-for-bit the oracle's step contract */
 #define PIC_FP32 1 /* FP32 cell + offset particle state, FP64 field solve and diagnostics */
@@ -134,6 +138,8 @@ typedef struct pic_diag_out {
   double p_coll_e, p_coll_i;                      /* 1 - exp(-nu_max dt) (§3.5) */
   double cfl_max;                                 /* max |vx| dt/dx over electrons (§1, §3.5) */
   double lambda_d, dx_over_lambda_d, n_debye;     /* §3.5 (readings C-19, C-20) */
+  double mean_energy_e_ev;                        /* mean kinetic energy of all electrons
+                                                     now (runaway check of PIC_WARN_UNSTABLE) */
   int32_t status;                                 /* sticky device status (PIC_OK or error) */
 } pic_diag_out;
 
@@ -161,7 +167,9 @@ int pic_sync(pic_handle* h);
  * step running beside it in the same launch).  Same results as pic_step. */
 int pic_step_profiled(pic_handle* h, int64_t n_steps, double* ms_out);
 
-/* Synchronise and reduce the accumulators into physical diagnostics (host side). */
+/* Synchronise and reduce the accumulators into physical diagnostics (host side).  Returns
+ * the sticky device status if it is an error, else PIC_WARN_UNSTABLE when the run is
+ * numerically unstable (see PIC_WARN_UNSTABLE; §3.5 names such runs), else PIC_OK. */
 int pic_diag(pic_handle* h, pic_diag_out* out);
 
 /* Copy one species' particles to host arrays of length >= capacity; *n_out = count.
@@ -352,16 +360,40 @@ int pic_mlp_gradients(pic_mlp* m, const float* x, const float* t, int32_t n, flo
  * batch's loss before the step is returned (synchronises); otherwise only enqueued. */
 int pic_mlp_train_step(pic_mlp* m, const float* x, const float* t, int32_t n, float lr,
                        float* loss);
+/* Copy an intermediate array of the last pic_mlp_forward / _gradients / _train_step call to
+ * a HOST buffer, first n rows (n <= the rows of that call), row-major: the values each
+ * kernel stage consumed or produced, so that a test can check every stage on its own inputs.
+ * BF16 arrays are raw 16-bit patterns.  Columns: X 16 (7 inputs, zero padded), Y / dY / dYh
+ * 192, all others 256.  The backward arrays (which >= PIC_MLP_ACT_DY) need a last call that
+ * ran the backward pass.  Synchronises.  PIC_ERR_PARAM for another `which`, n out of range,
+ * or a backward array after a forward-only call. */
+#define PIC_MLP_ACT_X 0     /* BF16 inputs */
+#define PIC_MLP_ACT_Z1 1    /* FP32 pre-activations of layer 1 (bias added) */
+#define PIC_MLP_ACT_H1 2    /* BF16 GELU(Z1) */
+#define PIC_MLP_ACT_Z2 3    /* FP32 pre-activations of layer 2 */
+#define PIC_MLP_ACT_H2 4    /* BF16 GELU(Z2) */
+#define PIC_MLP_ACT_Y 5     /* FP32 outputs */
+#define PIC_MLP_ACT_DY 6    /* FP32 loss gradient 2 (Y - T) / (n 192) */
+#define PIC_MLP_ACT_DYH 7   /* its BF16 copy */
+#define PIC_MLP_ACT_DZ2 8   /* FP32 gradient at Z2: (dYh W3) GELU'(Z2) */
+#define PIC_MLP_ACT_DZ2H 9  /* its BF16 copy */
+#define PIC_MLP_ACT_DZ1 10  /* FP32 gradient at Z1: (dZ2h W2) GELU'(Z1) */
+#define PIC_MLP_ACT_DZ1H 11 /* its BF16 copy */
+int pic_mlp_get_activations(pic_mlp* m, int32_t which, int32_t n, void* host);
 void pic_mlp_free(pic_mlp* m);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free field solve.  The paper has no counterpart: it is a deployment variant of
  * the field solve of §2 step 2 (exact discrete Green's function, reading C-23) for callers
- * that cannot allocate device memory -- code recorded into a CUDA graph by stream capture,
- * processes whose caching allocator owns the whole device, or library users with no
- * workspace to hand over.  It uses no handle, no workspace and no allocating call (CUDA or
- * otherwise): its one scratch array, the int128 sums S_j (16 bytes per node), is a
- * file-scope device array of PIC_FIELD_STATIC_MAX_CELLS + 1 nodes (1 MiB) inside libpic.so.
+ * that cannot allocate device memory: processes whose caching allocator has already reserved
+ * the device's free memory (a further cudaMalloc fails or forces the pool to release
+ * memory), code on latency-critical paths that must not call cudaMalloc / cudaFree (they can
+ * synchronise the whole device and stall other streams), and plug-ins whose host gives them
+ * device pointers but no allocator or workspace to hand over.  It uses no handle, no
+ * workspace and no allocating call (CUDA or otherwise): its one scratch array, the int128
+ * sums S_j (16 bytes per node), is a file-scope device array of
+ * PIC_FIELD_STATIC_MAX_CELLS + 1 nodes (1 MiB) inside libpic.so, held by every device that
+ * loads the library until the process exits.
  *
  * charge_e, charge_i  DEVICE int64 arrays [n_cells + 1], the charge counts at the nodes in
  *                     units of 2^-32 superparticles (the layout pic_get_grid returns).
@@ -374,20 +406,24 @@ void pic_mlp_free(pic_mlp* m);
  *
  * All four arrays must be device (or managed) memory of the current device, 8-byte aligned,
  * and must not overlap each other.  For the same counts and voltage the result is bit for
- * bit that of pic_solve_field / pic_get_grid of a handle with the same gap, weight, area and
- * n_cells.  Nothing has to be zeroed beforehand: every scratch element read is written
- * earlier in the same launch.
+ * bit that of pic_solve_field / pic_get_grid of a PIC_FP64 handle with the same gap, weight,
+ * area and n_cells.  A PIC_FP32 handle's field solve multiplies by rounded reciprocals where
+ * this one divides, so its phi and E agree with these within one unit in the last place.
+ * Nothing has to be zeroed beforehand: every scratch element read is written earlier in the
+ * same launch.
  *
  * Returns PIC_ERR_SCRATCH for n_cells > PIC_FIELD_STATIC_MAX_CELLS (nothing is launched),
  * PIC_ERR_PARAM for other invalid arguments (non-device or misaligned pointer, N < 2,
  * non-positive or non-finite sizes), PIC_ERR_CUDA if the set-up or the launch fails.
  * Enqueued only: the results are ready when the stream reaches them.
  *
- * Set-up: the first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call outside stream capture.
- * Concurrency: all calls on one device share the scratch array, so two calls whose launches
- * can run at the same time (different streams, or parallel branches of one graph) race and
- * give wrong results.  Order them on one stream or with events.
+ * Set-up: the first call on each device, with that device current, looks up the scratch
+ * array's device address (cudaGetSymbolAddress) and caches it for later calls; that first
+ * call should come before any stream capture.  The cached address belongs to the device's
+ * current context: after cudaDeviceReset, unload and reload the library before calling again.
+ * Concurrency: all calls on one device share the scratch array, which keeps the last call's
+ * contents, so two calls whose launches can run at the same time (on different streams) race
+ * and give wrong results.  Order them on one stream or with events.
  * --------------------------------------------------------------------------------------- */
 #define PIC_FIELD_STATIC_MAX_CELLS 65536
 int pic_field_solve_static(const int64_t* charge_e, const int64_t* charge_i, int32_t n_cells,

@@ -717,21 +717,29 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   PIC_CUDA(cudaMemcpy(fedf.data(), K.fedf, sizeof(uint64_t) * fedf.size(), cudaMemcpyDeviceToHost));
   PIC_CUDA(cudaMemcpy(out->counters, K.counters, sizeof(uint64_t) * kNumCounters, cudaMemcpyDeviceToHost));
   PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
-  // max |vx| over the electrons for the CFL number
+  // max |vx| over the electrons for the CFL number, and their sum of |v|^2 for the mean
+  // energy of the runaway check
   PIC_CUDA(cudaMemsetAsync(&K.st->vmax_bits, 0, sizeof(unsigned long long), h->stream));
-  if (is_fp32(h))  // straight from the FP32 state, in cells per step
+  PIC_CUDA(cudaMemsetAsync(&K.st->v2sum, 0, sizeof(double), h->stream));
+  if (is_fp32(h)) {  // straight from the FP32 state, in cells per step
     PIC_CUDA(launch_max_abs_vx32(K, 0, s.n[0], &K.st->vmax_bits, h->stream));
-  else
+    PIC_CUDA(launch_sum_v2_32(K, 0, s.n[0], &K.st->v2sum, h->stream));
+  } else {
     PIC_CUDA(launch_max_abs(K.vx[0], s.n[0], &K.st->vmax_bits, h->stream));
+    PIC_CUDA(launch_sum_v2(K, 0, s.n[0], &K.st->v2sum, h->stream));
+  }
   unsigned long long vbits = 0;
+  double v2sum = 0.0;
   PIC_CUDA(cudaStreamSynchronize(h->stream));
   PIC_CUDA(cudaMemcpy(&vbits, &K.st->vmax_bits, sizeof vbits, cudaMemcpyDeviceToHost));
+  PIC_CUDA(cudaMemcpy(&v2sum, &K.st->v2sum, sizeof v2sum, cudaMemcpyDeviceToHost));
   double vmax;
   if (is_fp32(h)) {
     float f;
     const uint32_t b = (uint32_t)vbits;
     std::memcpy(&f, &b, sizeof f);
     vmax = (double)f * K.to_si_v;
+    v2sum *= K.to_si_v * K.to_si_v;
   } else {
     std::memcpy(&vmax, &vbits, sizeof vmax);
   }
@@ -798,8 +806,13 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   out->lambda_d = lam;
   out->dx_over_lambda_d = d.dx / lam;
   out->n_debye = std::isfinite(lam) ? n_c * A * lam / W : INFINITY;  // reading C-20
+  // runaway check: mean electron kinetic energy against the largest energy the drive can
+  // give (e |V_rf|), with a floor for undriven runs
+  out->mean_energy_e_ev = s.n[0] > 0 ? (v2sum / (double)s.n[0]) * (0.5 * kMe / kQe) : 0.0;
   if (rc != PIC_OK) return rc;
-  return out->omega_pe_dt_max > 2.0 ? PIC_WARN_UNSTABLE : PIC_OK;
+  const double runaway_ev = std::max(std::fabs(p.v_rf_amp_v), PIC_RUNAWAY_FLOOR_EV);
+  const bool unstable = out->omega_pe_dt_max > 2.0 || !(out->mean_energy_e_ev <= runaway_ev);
+  return unstable ? PIC_WARN_UNSTABLE : PIC_OK;
 }
 
 // ------------------------------------------------------------ checkpoint / resume
@@ -1241,7 +1254,9 @@ const char* pic_strerror(int code) {
     case PIC_ERR_TIMEOUT: return "a bounded device wait ran out (staged data never arrived)";
     case PIC_ERR_SCRATCH:
       return "n_cells above PIC_FIELD_STATIC_MAX_CELLS, the static scratch of pic_field_solve_static";
-    case PIC_WARN_UNSTABLE: return "omega_pe*dt above the leapfrog stability bound 2";
+    case PIC_WARN_UNSTABLE:
+      return "numerically unstable: omega_pe*dt above the leapfrog bound 2, or runaway "
+             "electron energy";
     default: return "unknown code";
   }
 }

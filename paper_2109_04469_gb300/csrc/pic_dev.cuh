@@ -105,6 +105,7 @@ struct DevState {
   int status;           // sticky kSt* bits
   long long steps_avg;  // steps added to the RF-average accumulators
   unsigned long long vmax_bits;  // scratch of the |vx| maximum reduction
+  double v2sum;                  // scratch of the electrons' sum of |v|^2 (diagnostics)
   unsigned id_snap[2];           // next_id at the start of the current step's particle pass
 };
 

@@ -850,6 +850,26 @@ __global__ void k_max_abs_vx32(DevCtx K, int s, long long n, unsigned long long*
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, (unsigned long long)m);
 }
 
+// Sum of vx^2 + vy^2 + vz^2 over the first n particles of species s, in (cells per step)^2,
+// accumulated in double: one double atomic per block (a diagnostic only).
+__global__ void k_sum_v2_32(DevCtx K, int s, long long n, double* out) {
+  __shared__ double ws[kWarps32];
+  double acc = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double a = K.ov[s][q].y, b = K.fvy[s][q], c = K.fvz[s][q];
+    acc += (a * a + b * b) + c * c;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps32; ++w) t += ws[w];
+    if (t != 0.0) atomicAdd(out, t);
+  }
+}
+
 // FP32 cell units -> FP64 SI state, for pic_get_particles and the diagnostics.
 __global__ void k_to_fp64(DevCtx K, int s, long long n) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1228,6 +1248,14 @@ cudaError_t launch_max_abs_vx32(const DevCtx& K, int species, long long n,
   if (n <= 0) return cudaSuccess;
   const long long want = (n + 255) / 256;
   k_max_abs_vx32<<<(unsigned)(want < 1024 ? want : 1024), 256, 0, s>>>(K, species, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_v2_32(const DevCtx& K, int species, long long n, double* out,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + kBlock - 1) / kBlock;
+  k_sum_v2_32<<<(unsigned)(want < 1024 ? want : 1024), kBlock, 0, s>>>(K, species, n, out);
   return cudaGetLastError();
 }
 

@@ -132,6 +132,30 @@ __global__ void k_max_abs(const double* __restrict__ v, long long n, unsigned lo
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
+// Sum of vx^2 + vy^2 + vz^2 over the first n particles of species s (FP64 SI state): one
+// double atomic per block, so the last bits depend on the block order (a diagnostic only).
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+  return t;  // valid in thread 0
+}
+
+__global__ void k_sum_v2(DevCtx K, int s, long long n, double* out) {
+  double acc = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double a = K.vx[s][q], b = K.vy[s][q], c = K.vz[s][q];
+    acc += (a * a + b * b) + c * c;
+  }
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0 && t != 0.0) atomicAdd(out, t);
+}
+
 // Stand-alone field solve for the current step (after init, set_particles, set_step, or on
 // request); touches no accumulator.
 // Block f of F writes nodes [nx f / F, nx (f + 1) / F), like the field blocks of a step.
@@ -531,6 +555,14 @@ cudaError_t launch_max_abs(const double* v, long long n, unsigned long long* out
   const long long want = (n + 255) / 256;
   const unsigned grid = (unsigned)(want < 1024 ? want : 1024);
   k_max_abs<<<grid, 256, 0, s>>>(v, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_v2(const DevCtx& K, int species, long long n, double* out,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  k_sum_v2<<<(unsigned)(want < 1024 ? want : 1024), 256, 0, s>>>(K, species, n, out);
   return cudaGetLastError();
 }
 

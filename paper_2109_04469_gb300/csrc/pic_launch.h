@@ -23,6 +23,12 @@ cudaError_t launch_max_abs_vx32(const DevCtx& K, int species, long long n,
                                 unsigned long long* out, cudaStream_t s);
 cudaError_t launch_max_abs(const double* v, long long n, unsigned long long* out,
                            cudaStream_t s);
+// sum over the first n particles of species s of vx^2 + vy^2 + vz^2 (the handle's velocity
+// units), added to *out
+cudaError_t launch_sum_v2(const DevCtx& K, int species, long long n, double* out,
+                          cudaStream_t s);
+cudaError_t launch_sum_v2_32(const DevCtx& K, int species, long long n, double* out,
+                             cudaStream_t s);
 int push_fp64_blocks_per_sm(int nx);
 // raise the dynamic shared-memory limit of the grid-sized kernels for nx nodes
 cudaError_t configure_kernels(int nx);

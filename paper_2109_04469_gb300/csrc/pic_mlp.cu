@@ -398,7 +398,9 @@ struct pic_mlp {
   float *P, *M, *V;  // parameters and Adam moments, flat layout
   __nv_bfloat16 *W1h, *W2h, *W2t, *W3h, *W3t;
   __nv_bfloat16 *Xh, *Xt, *H1h, *H1t, *H2h, *H2t, *dYh, *dYt, *dZh, *dZt;
-  float *Z1, *Z2, *Y, *dY, *dZ, *gW1, *gW2t, *gW3t, *gb1, *gb2, *gb3;
+  float *Z1, *Z2, *Y, *dY, *dZ, *dZ1, *gW1, *gW2t, *gW3t, *gb1, *gb2, *gb3;
+  int last_n = 0;        // rows of the last forward pass
+  int last_backward = 0; // 1 if the last call also ran the backward pass
   double* rowloss;
   int* err;
 };
@@ -432,6 +434,7 @@ void mlp_carve(pic_mlp* m, char* base, int bmax, size_t* total) {
   m->Y = c.take<float>(B * kOut);
   m->dY = c.take<float>(B * kOut);
   m->dZ = c.take<float>(B * kHid);
+  m->dZ1 = c.take<float>(B * kHid);
   m->gW1 = c.take<float>((size_t)kHid * kInP);
   m->gW2t = c.take<float>((size_t)kHid * kHid);
   m->gW3t = c.take<float>((size_t)kHid * kOut);
@@ -505,16 +508,16 @@ cudaError_t mlp_backward(pic_mlp* m, const float* t, int B) {
   e = launch_gemm(m->H1t, m->dZt, m->gW2t, kHid, kHid, B, kHid, m->err, s);
   if (e != cudaSuccess) return e;
   k_colsum<<<1, kHid, 0, s>>>(m->dZ, B, kHid, m->gb2);
-  // dZ1 = (dZ2 W2) GELU'(Z1)
+  // dZ1 = (dZ2 W2) GELU'(Z1), FP32 into its own buffer (dZ2 stays readable)
   GemmEpi g1 = g2;
   g1.Zin = m->Z1;
   g1.H = nullptr;
-  e = launch_gemm(m->dZh, m->W2t, m->dZ, B, kHid, kHid, kHid, m->err, s, g1);
+  e = launch_gemm(m->dZh, m->W2t, m->dZ1, B, kHid, kHid, kHid, m->err, s, g1);
   if (e != cudaSuccess) return e;
   // dW1 [256 x 16] = dZ1^T X
   e = launch_gemm(m->dZt, m->Xt, m->gW1, kHid, kInP, B, kInP, m->err, s);
   if (e != cudaSuccess) return e;
-  k_colsum<<<1, kHid, 0, s>>>(m->dZ, B, kHid, m->gb1);
+  k_colsum<<<1, kHid, 0, s>>>(m->dZ1, B, kHid, m->gb1);
   return cudaGetLastError();
 }
 
@@ -652,6 +655,8 @@ int pic_mlp_set_params(pic_mlp* m, const float* params) {
 int pic_mlp_forward(pic_mlp* m, const float* x, int32_t n, float* y) {
   if (!m || !x || !y || n < 1 || n > m->bmax) return PIC_ERR_PARAM;
   const int Bp = (n + 127) / 128 * 128;
+  m->last_n = n;
+  m->last_backward = 0;
   if (mlp_forward(m, x, n, Bp) != cudaSuccess ||
       cudaMemcpyAsync(y, m->Y, sizeof(float) * (size_t)n * kOut, cudaMemcpyDeviceToDevice,
                       m->stream) != cudaSuccess) {
@@ -664,6 +669,8 @@ int pic_mlp_forward(pic_mlp* m, const float* x, int32_t n, float* y) {
 int pic_mlp_gradients(pic_mlp* m, const float* x, const float* t, int32_t n, float* grads,
                       float* loss) {
   if (!m || !x || !t || !grads || n < 128 || n % 128 || n > m->bmax) return PIC_ERR_PARAM;
+  m->last_n = n;
+  m->last_backward = 1;
   if (mlp_forward(m, x, n, n) != cudaSuccess || mlp_backward(m, t, n) != cudaSuccess) {
     (void)cudaGetLastError();
     return PIC_ERR_CUDA;
@@ -700,6 +707,8 @@ int pic_mlp_gradients(pic_mlp* m, const float* x, const float* t, int32_t n, flo
 int pic_mlp_train_step(pic_mlp* m, const float* x, const float* t, int32_t n, float lr,
                        float* loss) {
   if (!m || !x || !t || n < 128 || n % 128 || n > m->bmax || !(lr > 0.0f)) return PIC_ERR_PARAM;
+  m->last_n = n;
+  m->last_backward = 1;
   if (mlp_forward(m, x, n, n) != cudaSuccess || mlp_backward(m, t, n) != cudaSuccess) {
     (void)cudaGetLastError();
     return PIC_ERR_CUDA;
@@ -727,6 +736,50 @@ int pic_mlp_train_step(pic_mlp* m, const float* x, const float* t, int32_t n, fl
                                       1, kOut, lr, b1, b2, eps, c1, c2, nullptr, 0, nullptr);
   if (cudaGetLastError() != cudaSuccess) return PIC_ERR_CUDA;
   return loss ? mlp_loss(m, n, loss) : PIC_OK;
+}
+
+int pic_mlp_get_activations(pic_mlp* m, int32_t which, int32_t n, void* host) {
+  if (!m || !host || which < 0 || which > PIC_MLP_ACT_DZ1H || n < 1 || n > m->last_n)
+    return PIC_ERR_PARAM;
+  if (which >= PIC_MLP_ACT_DY && !m->last_backward) return PIC_ERR_PARAM;
+  const void* src = nullptr;
+  size_t elem = 4, cols = kHid;
+  switch (which) {
+    case PIC_MLP_ACT_X: src = m->Xh; elem = 2; cols = kInP; break;
+    case PIC_MLP_ACT_Z1: src = m->Z1; break;
+    case PIC_MLP_ACT_H1: src = m->H1h; elem = 2; break;
+    case PIC_MLP_ACT_Z2: src = m->Z2; break;
+    case PIC_MLP_ACT_H2: src = m->H2h; elem = 2; break;
+    case PIC_MLP_ACT_Y: src = m->Y; cols = kOut; break;
+    case PIC_MLP_ACT_DY: src = m->dY; cols = kOut; break;
+    case PIC_MLP_ACT_DYH: src = m->dYh; elem = 2; cols = kOut; break;
+    case PIC_MLP_ACT_DZ2: src = m->dZ; break;
+    case PIC_MLP_ACT_DZ2H: src = m->dZh; elem = 2; break;
+    case PIC_MLP_ACT_DZ1: src = m->dZ1; break;
+    default: break;  // PIC_MLP_ACT_DZ1H: kept transposed [256][n] for the dW1 product
+  }
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return PIC_ERR_CUDA;
+  }
+  if (src) {
+    if (cudaMemcpy(host, src, elem * cols * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return PIC_ERR_CUDA;
+    }
+    return PIC_OK;
+  }
+  const int ldt = m->last_n;  // the backward pass ran on exactly last_n rows
+  std::vector<uint16_t> t((size_t)kHid * ldt);
+  if (cudaMemcpy(t.data(), m->dZt, sizeof(uint16_t) * t.size(), cudaMemcpyDeviceToHost) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return PIC_ERR_CUDA;
+  }
+  uint16_t* out = static_cast<uint16_t*>(host);
+  for (int b = 0; b < n; ++b)
+    for (int j = 0; j < kHid; ++j) out[(size_t)b * kHid + j] = t[(size_t)j * ldt + b];
+  return PIC_OK;
 }
 
 void pic_mlp_free(pic_mlp* m) { delete m; }

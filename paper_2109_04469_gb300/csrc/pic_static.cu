@@ -1,14 +1,16 @@
 // pic_field_solve_static: the field solve of §2 step 2 (exact discrete Green's function,
 // reading C-23) on caller-owned device arrays, for callers that must not allocate device
-// memory at all -- code running inside CUDA stream capture, under a caching allocator that
-// owns every byte of the device, or in a process that has no workspace to hand over.
+// memory at all -- a process whose caching allocator has reserved the device's free memory,
+// a latency-critical path that must not call cudaMalloc / cudaFree (they can synchronise the
+// device), or a plug-in that is handed device pointers but no allocator or workspace.
 //
 // Its one scratch array (the integer sums S_j of the Green's function, one per node) lives in
 // a file-scope __device__ array of fixed size instead of shared memory or a workspace, so
 // grids larger than the shared-memory field solve of the simulation handle can be solved.
-// The arithmetic is the simulation's field solve: exact int128 sums, then the same rounded
-// FP64 operations in the same order, so phi and E agree bit for bit with pic_solve_field for
-// the same charge and drive voltage.
+// The arithmetic is the FP64 simulation's field solve: exact int128 sums, then the same
+// rounded FP64 operations in the same order, so phi and E agree bit for bit with
+// pic_solve_field of a PIC_FP64 handle for the same charge and drive voltage (a PIC_FP32
+// handle multiplies by rounded reciprocals instead of dividing: within one ulp).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -93,7 +95,9 @@ __global__ void __launch_bounds__(kStaticThreads, 1) k_field_static(StaticField 
 std::mutex g_scratch_mutex;
 __int128* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_field_scratch on the current device, looked up once per device.
+// Device address of g_field_scratch on the current device, looked up once per device (with
+// that device current) and cached for the life of the process; a cudaDeviceReset invalidates
+// it, which the header tells callers.
 cudaError_t scratch_address(__int128** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

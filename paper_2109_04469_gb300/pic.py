@@ -57,6 +57,7 @@ class PicDiagOut(C.Structure):
         ("omega_pe_dt", C.c_double), ("omega_pe_dt_max", C.c_double),
         ("p_coll_e", C.c_double), ("p_coll_i", C.c_double), ("cfl_max", C.c_double),
         ("lambda_d", C.c_double), ("dx_over_lambda_d", C.c_double), ("n_debye", C.c_double),
+        ("mean_energy_e_ev", C.c_double),
         ("status", C.c_int32),
     ]
 
@@ -111,6 +112,7 @@ def lib() -> C.CDLL:
                 "pic_mlp_forward": (C.c_int, [P, P, C.c_int32, P]),
                 "pic_mlp_gradients": (C.c_int, [P, P, P, C.c_int32, P, C.POINTER(C.c_float)]),
                 "pic_mlp_train_step": (C.c_int, [P, P, P, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
+                "pic_mlp_get_activations": (C.c_int, [P, C.c_int32, C.c_int32, P]),
                 "pic_mlp_free": (None, [P]),
                 "pic_checkpoint_bytes": (C.c_int, [P, C.POINTER(C.c_size_t)]),
                 "pic_checkpoint_save": (C.c_int, [P, P, C.c_size_t]),
@@ -488,6 +490,22 @@ class Mlp:
                                         float(lr), C.byref(loss) if want_loss else None),
                "pic_mlp_train_step")
         return loss.value if want_loss else None
+
+    ACTS = {"X": (0, 16, True), "Z1": (1, 256, False), "H1": (2, 256, True),
+            "Z2": (3, 256, False), "H2": (4, 256, True), "Y": (5, 192, False),
+            "dY": (6, 192, False), "dYh": (7, 192, True), "dZ2": (8, 256, False),
+            "dZ2h": (9, 256, True), "dZ1": (10, 256, False), "dZ1h": (11, 256, True)}
+
+    def activations(self, name: str, n: int) -> np.ndarray:
+        """An intermediate array of the last call (pic_mlp_get_activations), first n rows, as
+        float64 (BF16 arrays decoded exactly)."""
+        which, cols, is_bf16 = self.ACTS[name]
+        buf = np.zeros((n, cols), dtype=np.uint16 if is_bf16 else np.float32)
+        _check(lib().pic_mlp_get_activations(self._h, which, n, _ptr(buf)),
+               "pic_mlp_get_activations")
+        if is_bf16:
+            return (buf.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return buf.astype(np.float64)
 
     def close(self):
         if getattr(self, "_h", None):

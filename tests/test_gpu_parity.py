@@ -124,6 +124,9 @@ def test_200_steps_parity(variant):
         assert np.allclose(d_g[k], d_r[k], rtol=1e-13, atol=0), k
     for k in ("ion_flux", "omega_pe_dt", "lambda_d", "cfl_max", "p_coll_e", "p_coll_i"):
         assert abs(d_g[k] - d_r[k]) <= 1e-12 * abs(d_r[k]), k
+    # a sum over the electrons in another order: rounding differences only
+    assert abs(d_g["mean_energy_e_ev"] - d_r["mean_energy_e_ev"]) <= 1e-11 * d_r["mean_energy_e_ev"]
+    assert d_g["return_code"] == int(d_r["unstable"])
     sim.close()
 
 

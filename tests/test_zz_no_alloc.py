@@ -1,11 +1,15 @@
-"""pic_field_solve_static, the allocation-free field solve (§2 step 2, reading C-23), against
-the simulation handle's field solve (pic_solve_field / pic_get_grid) and, at the largest grid
-its static scratch holds, against the FP64 oracle.
+"""pic_field_solve_static, the allocation-free field solve (§2 step 2, reading C-23), for
+callers that cannot allocate device memory (a caching allocator holding the device's free
+memory, paths that must not call cudaMalloc, plug-ins without an allocator), against the
+simulation handle's field solve (pic_solve_field / pic_get_grid) and, at the largest grid its
+static scratch holds, against the FP64 oracle.
 
-Both sides sum the same exact int128 Green's-function terms and round the same FP64
-operations in the same order, so the bar is bit-identical phi and E; the relative tolerance
-2^-50 of the field's scale is asserted first so a failure reports its size.  Collected last
-(file name) so it also runs after every other GPU test in the same process.
+Against a PIC_FP64 handle both sides sum the same exact int128 Green's-function terms and
+round the same FP64 operations in the same order, so the bar is bit-identical phi and E; the
+relative tolerance 2^-50 of the field's scale is asserted first so a failure reports its
+size.  A PIC_FP32 handle multiplies by rounded reciprocals where this entry point divides:
+the bar there is one unit in the last place.  Collected last (file name) so it also runs
+after every other GPU test in the same process.
 """
 import numpy as np
 import pytest
@@ -64,6 +68,30 @@ def test_two_calls_in_a_row_match_the_handle_solve():
     torch.cuda.synchronize()
     for k, (g, (phi, E)) in enumerate(zip(grids, outs)):
         _check(phi.cpu().numpy(), E.cpu().numpy(), g["phi"], g["E"], f"call {k}")
+    sim.close()
+
+
+def test_fp32_handle_field_within_one_ulp():
+    """A PIC_FP32 handle solves the same exact sums but multiplies by the reciprocals of
+    N dx, 2 N dx and N; each of phi and E then differs from the divided value by at most
+    one unit in the last place."""
+    cfg = workloads.params("ccp_5pa_150v_128c", precision=pic.PIC_FP32)
+    nc, nx = cfg["n_cells"], cfg["n_cells"] + 1
+    sim = pic.Simulation(cfg)
+    phi = torch.empty(nx, dtype=torch.float64, device="cuda")
+    E = torch.empty(nx, dtype=torch.float64, device="cuda")
+    for n in (25, 7):
+        sim.step(n)
+        sim.sync()
+        g = sim.grid()
+        rc = pic.field_solve_static(_dev(g["Ce"]), _dev(g["Ci"]), nc, cfg["gap_m"],
+                                    cfg["weight"], cfg["area_m2"], float(g["phi"][0]), phi, E)
+        assert rc == 0
+        torch.cuda.synchronize()
+        for name, got, want in (("phi", phi.cpu().numpy(), g["phi"]), ("E", E.cpu().numpy(),
+                                                                      g["E"])):
+            ulp = np.maximum(np.spacing(np.abs(got)), np.spacing(np.abs(want)))
+            assert np.all(np.abs(got - want) <= ulp), (name, n)
     sim.close()
 
 
