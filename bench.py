@@ -91,23 +91,29 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+def profiled_value(kernel: str, workload: str, key: str):
+    """A figure from a committed ncu summary (profiles/<kernel>_<workload>.txt), if the sources
+    it was taken on are unchanged (their hash is recorded in the summary)."""
     path = os.path.join(PROFILE_DIR, f"{kernel}_{workload}.txt")
     if not os.path.exists(path):
         return None
     vals = {}
     for line in open(path):
-        if ":" in line:
+        if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     srcs = tuple(s.strip() for s in vals.get("sources", ",".join(PUSH_SOURCES)).split(","))
     if vals.get("source_sha256_16") != source_hash(srcs):
         return None
     try:
-        return float(vals["dram_bytes_per_launch_full_workload"])
-    except (KeyError, ValueError):
+        return float(vals[key].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    return profiled_value(kernel, workload, "dram_bytes_per_launch_full_workload")
 
 
 class ClockSampler:
@@ -382,6 +388,31 @@ def measure(pcfg: dict, precision: str, args, torch, dist, local_rank: int,
     return out
 
 
+def fp64_pipe_roofline(parts_per_launch: float, launch_ms: float, workload: str) -> dict:
+    """The FP64 particle pass against the axis that bounds it on GB300: FP64 operations per
+    second (DADD + DMUL + 2 DFMA per particle-step, from the committed ncu counters of the
+    unchanged kernel) over the pipe rate measured live by pic_fp64_rate (separate multiplies
+    and adds, the FP64 path's own mix)."""
+    from paper_2109_04469_gb300 import pic
+
+    peak_mix, peak_fma = pic.fp64_rate()
+    inst = profiled_value("push_fp64", workload, "fp64_pipe_inst_per_particle_step")
+    ops = profiled_value("push_fp64", workload, "fp64_ops_per_particle_step")
+    out = {"bound": "fp64", "peak": peak_mix, "peak_fma_flops": peak_fma,
+           "unit": "FP64-pipe instructions/s",
+           "peak_source": "measured live (pic_fp64_rate: separate multiplies and adds)",
+           "inst_per_particle_step": inst, "flops_per_particle_step": ops}
+    if inst is not None and ops is not None:
+        rate = parts_per_launch / (launch_ms / 1e3)
+        out["achieved"] = inst * rate
+        out["frac"] = out["achieved"] / peak_mix
+        out["flops_frac"] = ops * rate / peak_mix
+    else:
+        out["achieved"] = out["frac"] = None
+        out["note"] = "no ncu count of FP64 instructions for the current kernel sources"
+    return out
+
+
 def measure_ensemble(args, torch, dist, rank: int) -> dict:
     """The batched FP32 scan: args.ensemble_members uneven simulations (workloads.
     ensemble_members) advanced by one graph-replayed launch per step.  Its state is many GB,
@@ -552,7 +583,9 @@ def profile_case(mode: str) -> None:
     if mode in ("fp32", "fp64"):
         prec = pic.PIC_FP32 if mode == "fp32" else pic.PIC_FP64
         sim = pic.Simulation(workloads.params("ccp_1pa_300v_400c", precision=prec))
-        sim.step(5)
+        for k in range(5):  # particles each step's pass starts from (for per-particle counts)
+            print("step", k, "particles", sum(sim.counts()))
+            sim.step(1)
         print("status", sim.sync())
     elif mode == "ens":  # 16 scan members (2.5e5-1e6 superparticles each)
         members = workloads.ensemble_members(16, per_run=(2.5e5, 1.0e6))
@@ -647,6 +680,9 @@ def main():
             "value": p / (t / 1e3), "ms_per_step": t / args.steps, "particles_ms": r["push_ms"],
             "roofline_frac_hbm": r["alg_bytes_per_launch"] / (r["push_ms"] / 1e3) / 1e9 / peak,
             "clocks": r["clocks"]}
+        if prec == "fp64":
+            line["fp64_plain"]["roofline_fp64_pipe"] = fp64_pipe_roofline(
+                r["parts"] / args.steps, r["push_ms"], args.workload)
         line[f"speedup_vs_{prec}"] = value / (p / (t / 1e3))
     if not args.no_ensemble:
         er = measure_ensemble(args, torch, dist, rank)

@@ -225,6 +225,14 @@ int pic_override_table(pic_handle* h, int species, const double* table, double n
 /* Derived constants (dt, dx, n_g, nu_max e/i, P_max e/i) into out[7]. */
 int pic_get_derived(pic_handle* h, double* out);
 
+/* Measured FP64 pipe rate of the current device (the paper has no counterpart: the roofline
+ * of the FP64 particle pass, which GB300's reduced FP64 rate bounds): rates[0] = FP64
+ * operations per second issued as separate multiplies and adds (the FP64 path's own mix,
+ * compiled without contraction), rates[1] = FP64 operations per second as fused multiply-adds
+ * (2 per instruction).  Two timed launches of about 10-20 ms each on cuda_stream (NULL:
+ * legacy default stream), 8 blocks per SM.  Synchronises. */
+int pic_fp64_rate(void* cuda_stream, double* rates);
+
 /* Release the handle (host memory only; the caller frees the workspace afterwards). */
 void pic_free(pic_handle* h);
 

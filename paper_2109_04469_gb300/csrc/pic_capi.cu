@@ -815,6 +815,20 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   return unstable ? PIC_WARN_UNSTABLE : PIC_OK;
 }
 
+int pic_fp64_rate(void* cuda_stream, double* rates) {
+  if (!rates) return PIC_ERR_PARAM;
+  int dev = 0, sms = 0;
+  PIC_CUDA(cudaGetDevice(&dev));
+  PIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  for (int k = 0; k < 2; ++k) {
+    double ms = 0.0, ops = 0.0;
+    PIC_CUDA(fp64_probe(k == 1, sms, 2048, &ms, &ops, s));
+    rates[k] = ms > 0.0 ? ops / (ms * 1e-3) : 0.0;
+  }
+  return PIC_OK;
+}
+
 // ------------------------------------------------------------ checkpoint / resume
 }  // extern "C"
 

@@ -566,6 +566,55 @@ cudaError_t launch_sum_v2(const DevCtx& K, int species, long long n, double* out
   return cudaGetLastError();
 }
 
+// FP64 pipe probe: kChains independent chains per thread of x <- x * a + b, either as a
+// separate multiply and add (what this translation unit's -fmad=false code issues: the
+// particle pass's mix) or as fused multiply-adds.  Each chain step is 2 FP64 operations.
+constexpr int kProbeChains = 8;
+__device__ double g_probe_sink;  // written only if the chains' sum hits an impossible value
+template <bool FMA>
+__global__ void __launch_bounds__(256) k_fp64_probe(int iters, double a, double b) {
+  double x[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) x[k] = 1e-3 * (double)(threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k)
+      x[k] = FMA ? __fma_rn(x[k], a, b) : __dadd_rn(__dmul_rn(x[k], a), b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) s += x[k];
+  if (s == 12345.678) g_probe_sink = s;  // never true for these inputs; keeps the chains live
+}
+
+cudaError_t fp64_probe(bool fma, int sms, int iters, double* ms, double* ops, cudaStream_t s) {
+  const unsigned grid = (unsigned)(8 * sms);
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return e;
+  }
+  float t = 0.0f;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    cudaEventRecord(a, s);
+    if (fma)
+      k_fp64_probe<true><<<grid, 256, 0, s>>>(iters, 0.999999, 1e-7);
+    else
+      k_fp64_probe<false><<<grid, 256, 0, s>>>(iters, 0.999999, 1e-7);
+    cudaEventRecord(b, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t;
+  *ops = 2.0 * (double)grid * 256.0 * (double)iters * kProbeChains;
+  return e;
+}
+
 cudaError_t configure_kernels(int nx) {
   cudaError_t e = raise_smem_limit(k_push_fp64, (int)push_smem_bytes(nx));
   if (e != cudaSuccess) return e;

@@ -30,6 +30,9 @@ cudaError_t launch_sum_v2(const DevCtx& K, int species, long long n, double* out
 cudaError_t launch_sum_v2_32(const DevCtx& K, int species, long long n, double* out,
                              cudaStream_t s);
 int push_fp64_blocks_per_sm(int nx);
+// FP64 pipe probe (8 x SMs blocks of 256 threads, iters steps of 8 chains): elapsed ms of the
+// timed launch and the FP64 operations it executed
+cudaError_t fp64_probe(bool fma, int sms, int iters, double* ms, double* ops, cudaStream_t s);
 // raise the dynamic shared-memory limit of the grid-sized kernels for nx nodes
 cudaError_t configure_kernels(int nx);
 // the placement launch's shared memory for nx nodes and nlist list owners

@@ -100,6 +100,7 @@ def lib() -> C.CDLL:
                 "pic_get_step": (C.c_int, [P, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
                 "pic_override_table": (C.c_int, [P, C.c_int, P, C.c_double]),
                 "pic_get_derived": (C.c_int, [P, P]),
+                "pic_fp64_rate": (C.c_int, [P, P]),
                 "pic_free": (None, [P]),
                 "pic_strerror": (C.c_char_p, [C.c_int]),
                 "pic_last_cuda_error": (C.c_char_p, []),
@@ -331,6 +332,17 @@ class Simulation:
             out[name] = np.array(v[:], dtype=np.uint64) if name == "counters" else v
         out["return_code"] = rc
         return out
+
+
+def fp64_rate(stream=None) -> tuple[float, float]:
+    """Measured FP64 operations per second of the device: (separate multiply + add, fused
+    multiply-add), from pic_fp64_rate."""
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = np.zeros(2)
+    _check(lib().pic_fp64_rate(C.c_void_p(s.cuda_stream), _ptr(out)), "pic_fp64_rate")
+    return float(out[0]), float(out[1])
 
 
 FIELD_STATIC_MAX_CELLS = 65536
