@@ -157,9 +157,10 @@ struct SurfOut {  // state after step 5; flags: bit 0 removed, bit 1 electron em
 // written to *em (this lane's slot in shared memory).
 template <int S>
 __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned step, long long p,
-                                          unsigned pid, int cell, float off, float vx, bool left,
+                                          int cell, float off, float vx, bool left,
                                           unsigned* sCe, unsigned long long* sCnt, Rec32* em) {
   const int nc = G->nc;
+  const unsigned pid = G->id[S][p];
   const float vy = G->fvy[S][p], vz = G->fvz[S][p];  // in flight during the draw below
   // the per-step block of the FP64 contract: its third word decides the surface event
   const U4 w = philox4x32_10(pid, step, ((unsigned)S << 30) | ((unsigned)kPurStep << 24), 0u,
@@ -218,9 +219,10 @@ struct CollOut {  // state after step 6; born: an ionization pair was written
 // slots in shared memory).
 template <int S>
 __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned step, long long p,
-                                          unsigned pid, int cell, float off, float vx,
-                                          unsigned cd, unsigned* sCe, unsigned* sCi,
-                                          unsigned long long* sCnt, Rec32* re, Rec32* ri) {
+                                          int cell, float off, float vx, unsigned cd,
+                                          unsigned* sCe, unsigned* sCi, unsigned long long* sCnt,
+                                          Rec32* re, Rec32* ri) {
+  const unsigned pid = G->id[S][p];  // one round trip with vy, vz
   float vy = G->fvy[S][p], vz = G->fvz[S][p];  // in flight during the draws below
   Stream sc(*G, S, kPurColl, pid, step);
   const U4 wp = philox4x32_10(sc.id, sc.step, sc.base | sc.block, 0u, sc.k0, sc.k1);
@@ -329,27 +331,31 @@ __device__ __forceinline__ void put_rec(float* list, size_t cap, long long slot,
 }
 
 // A warp's staging of one 128-particle tile (bulk-copy destination; 16-byte aligned fields).
+// Only the two words every particle needs are staged; the id is read by the rare paths.
 constexpr int kStages = 2;
 struct WarpTile {
   unsigned ccd[128];  // cell | countdown << 16
   float2 ov[128];     // off, vx
-  unsigned id[128];
 };
-// A particle whose countdown ran out (kind 1), or an electron of the EEPF window (kind 2),
-// queued until 32 of them (or the end of the warp's range) are handled together, one per
-// lane, so their scattered loads overlap.
+// The rare work of a particle, queued in particle order until 32 entries (or the end of the
+// warp's range) are handled together, one per lane, so that their scattered loads and
+// latency chains overlap: a particle that left the gap (surface, then for a survivor the
+// countdown, deposit and possibly a collision), a particle whose countdown ran out (a
+// null-collision candidate), or an electron of the EEPF cells.  pk = index | out << 31
+// (indices stay below 2^31); aux = cell | countdown << 16, the countdown decremented for this
+// step unless the particle left the gap, whose cell is kept as a signed 16-bit value
+// saturated at +-32767 (with at most 4096 cells a saturated cell is still outside after a
+// mirror reflection, so every surface decision is the unsaturated one's).
 struct Cand {
-  int p;         // index
-  unsigned ccd;  // cell | countdown << 16
+  unsigned pk;
+  unsigned aux;
   float off, vx;
-  unsigned id;
-  int kind;
 };
-constexpr int kCandQ = 64;  // up to 31 waiting + 32 from one row of 32 particles
+constexpr int kCandQ = 160;  // up to 31 waiting + 128 from one tile
 struct __align__(128) WarpPipe {  // one per warp, back to back in shared memory
   WarpTile t[kStages];
   unsigned long long bar[kStages];
-  Rec32 recE[32], recI[32];  // each lane's births of the current particle
+  Rec32 recE[32], recI[32];  // the lanes' births of the current drain
   Cand cq[kCandQ];
 };
 struct PipeCount {         // per-warp, warp-uniform, in registers
@@ -366,46 +372,82 @@ __device__ __forceinline__ bool in_eepf_cells(int nc, int cell) {
 }
 
 // Handle the first n queued entries (n <= 32, of nq queued), one per lane, in queue order
-// (particle order): for an expiry the collision and next countdown, then the EEPF sample of
-// the (collided) velocity, and the ionization pairs ranked by ballot into the warp's birth
-// lists.  The remaining nq - n entries move to the front of the queue.  Returns the pairs
-// born (the caller advances both birth-list offsets by it).
+// (particle order): for an outgoing particle the surface event (step 5) and, if it stays, its
+// countdown and deposit; then for an expired countdown the collision and next countdown
+// (step 6); then the EEPF sample of an electron in the centre window.  Holes and births are
+// ranked by ballot into the warp's lists (electrons: ionization pairs; ions: ion-induced
+// electrons).  The remaining nq - n entries move to the front of the queue.  Returns (holes,
+// births) listed: the caller advances hk by the first and ek (and, for electrons, ik) by the
+// second.
 template <int S>
-__device__ __noinline__ int drain32(const DevCtx* __restrict__ G, unsigned step, WarpPipe& P,
-                                    int n, int nq, unsigned* sCe, unsigned* sCi,
-                                    unsigned long long* sCnt, long long ek, long long ik) {
+__device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step, WarpPipe& P,
+                                     int n, int nq, unsigned* sCe, unsigned* sCi,
+                                     unsigned long long* sCnt, long long hk, long long ek,
+                                     long long ik) {
   __syncwarp();
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  bool born = false;
+  bool dead = false, born = false;
+  long long p = 0;
   if (lane < n) {
     const Cand c = P.cq[lane];
-    const int cell = (int)(c.ccd & 0xFFFFu);
-    float vx = c.vx;
-    if (c.kind == 1) {
-      const CollOut o = collide32<S>(G, step, c.p, c.id, cell, c.off, c.vx, c.ccd >> 16, sCe,
-                                     sCi, sCnt, &P.recE[lane], &P.recI[lane]);
-      G->ov[S][c.p] = make_float2(c.off, o.vx);
-      G->ccd[S][c.p] = (unsigned)cell | (o.cd << 16);
-      born = o.born != 0;
-      vx = o.vx;
+    p = (long long)(c.pk & 0x7FFFFFFFu);
+    int cell;
+    float off = c.off, vx = c.vx;
+    unsigned cd;
+    bool moved = false;
+    if (c.pk >> 31) {  // step 5: left the gap
+      cell = (int)(short)(c.aux & 0xFFFFu);
+      const bool left = cell < 0 || (cell == 0 && off == 0.0f);
+      const SurfOut r = surface32<S>(G, step, p, cell, off, vx, left, sCe, sCnt, &P.recE[lane]);
+      cell = r.cell;
+      off = r.off;
+      vx = r.vx;
+      dead = r.flags & 1;
+      born = (r.flags >> 1) & 1;  // an ion-induced electron (ions only)
+      cd = (c.aux >> 16) - 1u;  // this step's countdown decrement, for a survivor
+      if (!dead) deposit32(S == 0 ? sCe : sCi, cell, off);
+      moved = true;
+    } else {
+      cell = (int)(c.aux & 0xFFFFu);
+      cd = c.aux >> 16;
     }
-    if (S == 0 && in_eepf_cells(G->nc, cell)) eepf32(G, c.p, cell, c.off, vx, sCnt);
+    if (!dead) {
+      if ((cd & 0x7FFFu) == 0u) {  // the countdown ran out: step 6
+        const CollOut o = collide32<S>(G, step, p, cell, off, vx, cd, sCe, sCi, sCnt,
+                                       &P.recE[lane], &P.recI[lane]);
+        vx = o.vx;
+        cd = o.cd;
+        born = born || o.born != 0;  // an ionization pair (electrons only)
+        moved = true;
+      }
+      if (moved) {
+        G->ov[S][p] = make_float2(off, vx);
+        G->ccd[S][p] = ((unsigned)cell & 0xFFFFu) | (cd << 16);
+      }
+      if (S == 0 && in_eepf_cells(G->nc, cell)) eepf32(G, p, cell, off, vx, sCnt);
+    }
   }
-  int nb = 0;
-  if (S == 0) {
-    const unsigned mb = __ballot_sync(0xffffffffu, born);
-    if (born) {
-      const size_t cap = (size_t)G->nchunk_max * kChunk;
-      put_rec(G->feb[0], cap, ek + __popc(mb & lt), P.recE[lane]);
-      put_rec(G->fib, cap, ik + __popc(mb & lt), P.recI[lane]);
-    }
-    nb = __popc(mb);
+  const unsigned mh = __ballot_sync(0xffffffffu, dead);
+  const unsigned mb = __ballot_sync(0xffffffffu, born);
+  if (dead) G->hole_idx[S][hk + __popc(mh & lt)] = (int)p;
+  if (born) {
+    const size_t cap = (size_t)G->nchunk_max * kChunk;
+    put_rec(G->feb[S], cap, ek + __popc(mb & lt), P.recE[lane]);
+    if (S == 0) put_rec(G->fib, cap, ik + __popc(mb & lt), P.recI[lane]);
   }
   __syncwarp();
-  if (lane < nq - n) P.cq[lane] = P.cq[lane + n];  // n == 32 here: disjoint halves
-  __syncwarp();
-  return nb;
+  // the remaining nq - n entries move to the front (n == 32 here), 32 per round, every load
+  // of a round before its stores; nq and n are warp-uniform, so every lane runs every round
+  for (int i0 = 0; i0 < nq - n; i0 += 32) {
+    const int i = i0 + lane;
+    Cand c;
+    if (i < nq - n) c = P.cq[i + n];
+    __syncwarp();
+    if (i < nq - n) P.cq[i] = c;
+    __syncwarp();
+  }
+  return make_int2(__popc(mh), __popc(mb));
 }
 
 // Lane 0 starts the bulk copies of particles [t0, t0 + n) into the next stage (t0 is a
@@ -418,17 +460,125 @@ __device__ __forceinline__ void issue_tile(const DevCtx& K, WarpPipe& P, PipeCou
     WarpTile& T = P.t[st];
     const unsigned b4 = round16(4u * n), b8 = round16(8u * n);
     fence_proxy_async_smem();  // the lanes' earlier reads of this stage come first
-    mbar_arrive_expect_tx(&P.bar[st], 2u * b4 + b8);
+    mbar_arrive_expect_tx(&P.bar[st], b4 + b8);
     bulk_g2s(T.ccd, K.ccd[S] + t0, b4, &P.bar[st]);
     bulk_g2s(T.ov, K.ov[S] + t0, b8, &P.bar[st]);
-    bulk_g2s(T.id, K.id[S] + t0, b4, &P.bar[st]);
   }
   ++Q.issued;
 }
 
-// One warp walks particles [q, qe) of species S (q a multiple of 32) in 128-particle tiles,
-// kStages - 1 tiles in flight.  Holes and births go to the warp's lists at hk / ek / ik
-// (running offsets, warp-uniform).  Returns false if a staged tile never arrived.
+// Ranks in particle order of the flagged particles of a half tile (lane L holds particles
+// 2L and 2L + 1 of the half): m0, m1 the ballots of the lanes' first and second particles.
+// Returns the rank of the lane's first particle; the second one's is that plus its flag.
+__device__ __forceinline__ int half_rank(unsigned m0, unsigned m1, unsigned lt) {
+  return __popc(m0 & lt) + __popc(m1 & lt);
+}
+
+// Tile index of this lane's particle q (q = 2h + k: half h, k-th of the lane's two).
+__device__ __forceinline__ int tile_index(int q, int lane) {
+  return 64 * (q >> 1) + 2 * lane + (q & 1);
+}
+
+// One 128-particle tile of a warp's range.  Lane L holds particles 2L, 2L + 1 of each
+// 64-particle half of the tile: its two (cell | countdown) words are one 8-byte shared load
+// and one 8-byte global store, its two (off, vx) pairs one 16-byte load and store, all
+// contiguous across the warp.  Ranks in particle order (holes, births, queue slots) are two
+// ballots and two popcounts per half.  Expired countdowns and electrons of the EEPF cells
+// are appended to the warp's queue (drained between tiles).  FULL: the tile holds 128
+// particles of the range, so no bounds tests.
+template <int S, bool FULL>
+__device__ __forceinline__ void tile32_body(const DevCtx& K, long long tile, int nv,
+                                            const WarpTile& T, const float2* sE, unsigned* sCe,
+                                            unsigned* sCi, WarpPipe& P, int& nq, float& fin) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nc = K.nc;
+  int cell[4];
+  float off[4], vx[4];
+  unsigned cd[4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i0 = 64 * h + 2 * lane;
+    const uint2 cc = *reinterpret_cast<const uint2*>(&T.ccd[i0]);
+    const float4 o = *reinterpret_cast<const float4*>(&T.ov[i0]);
+    cell[2 * h] = (int)(cc.x & 0xFFFFu);
+    cell[2 * h + 1] = (int)(cc.y & 0xFFFFu);
+    cd[2 * h] = cc.x >> 16;
+    cd[2 * h + 1] = cc.y >> 16;
+    off[2 * h] = o.x;
+    vx[2 * h] = o.y;
+    off[2 * h + 1] = o.z;
+    vx[2 * h + 1] = o.w;
+  }
+  // steps 3-4: linear gather and leapfrog in cell units
+  bool out[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool valid = FULL || tile_index(q, lane) < nv;
+    if (!FULL && !valid) cell[q] = 0;  // staged words past nv are not this range's
+    const float2 e = sE[cell[q]];
+    vx[q] += e.x + off[q] * e.y;
+    off[q] += vx[q];
+    renorm(cell[q], off[q]);
+    if (FULL || valid) fin = fmaf(vx[q], 0.0f, fin);
+    out[q] = valid && ((unsigned)cell[q] >= (unsigned)nc ||
+                       (__float_as_uint(off[q]) | (unsigned)cell[q]) == 0u);
+  }
+  // step 6 for the particles still in the gap: the countdown to the next null-collision
+  // candidate, then the deposit (a collision changes neither cell nor offset).  Queued for the
+  // drain, in particle order: an outgoing particle (surface first, step 5), an expired
+  // countdown, an electron in the EEPF cells.
+  bool qd[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    qd[q] = out[q];
+    if ((FULL || tile_index(q, lane) < nv) && !out[q]) {
+      --cd[q];
+      deposit32(S == 0 ? sCe : sCi, cell[q], off[q]);
+      qd[q] = (cd[q] & 0x7FFFu) == 0u || (S == 0 && in_eepf_cells(nc, cell[q]));
+    }
+  }
+  unsigned* __restrict__ gccd = K.ccd[S] + tile;
+  float2* __restrict__ gov = K.ov[S] + tile;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i0 = 64 * h + 2 * lane;
+    const unsigned w0 = ((unsigned)cell[2 * h] & 0xFFFFu) | (cd[2 * h] << 16);
+    const unsigned w1 = ((unsigned)cell[2 * h + 1] & 0xFFFFu) | (cd[2 * h + 1] << 16);
+    const float4 o = make_float4(off[2 * h], vx[2 * h], off[2 * h + 1], vx[2 * h + 1]);
+    if (FULL || i0 + 1 < nv) {
+      *reinterpret_cast<uint2*>(gccd + i0) = make_uint2(w0, w1);
+      *reinterpret_cast<float4*>(gov + i0) = o;
+    } else if (i0 < nv) {
+      gccd[i0] = w0;
+      gov[i0] = make_float2(o.x, o.y);
+    }
+  }
+  if (__any_sync(0xffffffffu, qd[0] | qd[1] | qd[2] | qd[3])) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned m0 = __ballot_sync(0xffffffffu, qd[2 * h]);
+      const unsigned m1 = __ballot_sync(0xffffffffu, qd[2 * h + 1]);
+      const int r = nq + half_rank(m0, m1, lt);
+      const unsigned p0 = (unsigned)(tile + 64 * h + 2 * lane);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int q = 2 * h + k;
+        if (qd[q])
+          P.cq[r + (k ? (int)qd[2 * h] : 0)] =
+              Cand{(p0 + (unsigned)k) | ((unsigned)out[q] << 31),
+                   ((unsigned)max(-32767, min(32767, cell[q])) & 0xFFFFu) | (cd[q] << 16),
+                   off[q], vx[q]};
+      }
+      nq += __popc(m0) + __popc(m1);
+    }
+  }
+}
+
+// One warp walks particles [q, qe) of species S (q a multiple of 32) in 128-particle tiles
+// staged in shared memory by bulk copies, kStages - 1 tiles in flight.  Holes and births go
+// to the warp's lists at hk / ek / ik (running offsets, warp-uniform).  Returns false if a
+// staged tile never arrived.
 template <int S>
 __device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long long q,
                                             long long qe, const float2* sE, unsigned* sCe,
@@ -436,9 +586,6 @@ __device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long
                                             WarpPipe& P, PipeCount& Q, long long& hk,
                                             long long& ek, long long& ik) {
   const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const int nc = K.nc;
-  const size_t cap = (size_t)K.nchunk_max * kChunk;
   const DevCtx* __restrict__ G = K.self;
   const int ntiles = (int)((qe - q + 127) / 128);
   int nq = 0;          // queued entries (warp-uniform)
@@ -459,122 +606,26 @@ __device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long
       return false;
     }
     ++Q.waited;
-    const WarpTile& T = P.t[st];
     const long long tile = q + 128ll * t;
     const int nv = (int)min(128ll, qe - tile);  // particles of this tile
-    unsigned* __restrict__ gccd = K.ccd[S] + tile;
-    float2* __restrict__ gov = K.ov[S] + tile;
-    // Each lane owns particles 32 j + lane (j = 0..3), so the tile is walked in particle
-    // order j-major, lane-minor; the common path of the four runs interleaved.
-    // steps 3-4: linear gather and leapfrog in cell units
-    int cell[4];
-    float off[4], vx[4];
-    unsigned cd[4];
-    unsigned outm = 0u;  // bit j: particle j left the gap
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int ix = 32 * j + lane;
-      const bool valid = ix < nv;
-      const unsigned cc = T.ccd[ix];
-      const float2 ov = T.ov[ix];
-      cell[j] = valid ? (int)(cc & 0xFFFFu) : 0;  // staged entries past nv are not this range's
-      cd[j] = cc >> 16;
-      off[j] = ov.x;
-      vx[j] = ov.y;
-      const float2 e = sE[cell[j]];
-      vx[j] += e.x + off[j] * e.y;
-      off[j] += vx[j];
-      renorm(cell[j], off[j]);
-      if (valid) {
-        fin = fmaf(vx[j], 0.0f, fin);
-        if ((unsigned)cell[j] >= (unsigned)nc || (cell[j] == 0 && off[j] == 0.0f)) outm |= 1u << j;
-      }
-    }
-    // step 5 (rare): surfaces, holes and ion-induced electrons ranked in particle order
-    unsigned deadm = 0u;
-    if (__any_sync(0xffffffffu, outm != 0u)) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool out = (outm >> j) & 1u;
-        if (__any_sync(0xffffffffu, out)) {
-          const long long p = tile + 32 * j + lane;
-          bool dead = false, be = false;
-          if (out) {
-            const bool out_l = cell[j] < 0 || (cell[j] == 0 && off[j] == 0.0f);
-            const SurfOut r = surface32<S>(G, step, p, T.id[32 * j + lane], cell[j], off[j],
-                                           vx[j], out_l, sCe, sCnt, &P.recE[lane]);
-            cell[j] = r.cell;
-            off[j] = r.off;
-            vx[j] = r.vx;
-            dead = r.flags & 1;
-            be = (r.flags >> 1) & 1;
-          }
-          const unsigned mh = __ballot_sync(0xffffffffu, dead);
-          const unsigned me = __ballot_sync(0xffffffffu, be);
-          if (dead) K.hole_idx[S][hk + __popc(mh & lt)] = (int)p;
-          if (be) put_rec(K.feb[S], cap, ek + __popc(me & lt), P.recE[lane]);
-          hk += __popc(mh);
-          ek += __popc(me);
-          deadm |= (unsigned)dead << j;
-        }
-      }
-    }
-    // step 6: the countdown to the next null-collision candidate, then the deposit (the
-    // collision changes neither cell nor offset).  An expiry is queued (kind 1), as is an
-    // electron in the EEPF cells (kind 2); their velocity and countdown are rewritten by the
-    // drain, after the stores below.
-    unsigned expm = 0u, eepm = 0u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int ix = 32 * j + lane;
-      if (ix < nv && !((deadm >> j) & 1u)) {
-        --cd[j];
-        const bool ex = (cd[j] & 0x7FFFu) == 0u;
-        expm |= (unsigned)ex << j;
-        deposit32(S == 0 ? sCe : sCi, cell[j], off[j]);
-        if (S == 0 && !ex && in_eepf_cells(nc, cell[j])) eepm |= 1u << j;
-      }
-    }
-    if (nv == 128) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        gccd[32 * j + lane] = ((unsigned)cell[j] & 0xFFFFu) | (cd[j] << 16);
-        gov[32 * j + lane] = make_float2(off[j], vx[j]);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (32 * j + lane < nv) {
-          gccd[32 * j + lane] = ((unsigned)cell[j] & 0xFFFFu) | (cd[j] << 16);
-          gov[32 * j + lane] = make_float2(off[j], vx[j]);
-        }
-    }
-    if (__any_sync(0xffffffffu, (expm | eepm) != 0u)) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool qj = ((expm | eepm) >> j) & 1u;
-        const unsigned mq = __ballot_sync(0xffffffffu, qj);
-        if (mq) {
-          if (qj)
-            P.cq[nq + __popc(mq & lt)] =
-                Cand{(int)(tile + 32 * j + lane), ((unsigned)cell[j] & 0xFFFFu) | (cd[j] << 16),
-                     off[j], vx[j], T.id[32 * j + lane], ((expm >> j) & 1u) ? 1 : 2};
-          nq += __popc(mq);
-          if (nq >= 32) {
-            const int nb = drain32<S>(G, step, P, 32, nq, sCe, sCi, sCnt, ek, ik);
-            ek += nb;
-            ik += nb;
-            nq -= 32;
-          }
-        }
-      }
+    if (nv == 128)
+      tile32_body<S, true>(K, tile, 128, P.t[st], sE, sCe, sCi, P, nq, fin);
+    else
+      tile32_body<S, false>(K, tile, nv, P.t[st], sE, sCe, sCi, P, nq, fin);
+    while (nq >= 32) {  // the rare work, 32 entries at a time, in queue order
+      const int2 r = drain32<S>(G, step, P, 32, nq, sCe, sCi, sCnt, hk, ek, ik);
+      hk += r.x;
+      ek += r.y;
+      if (S == 0) ik += r.y;
+      nq -= 32;
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
   }
   if (nq > 0) {
-    const int nb = drain32<S>(G, step, P, nq, nq, sCe, sCi, sCnt, ek, ik);
-    ek += nb;
-    ik += nb;
+    const int2 r = drain32<S>(G, step, P, nq, nq, sCe, sCi, sCnt, hk, ek, ik);
+    hk += r.x;
+    ek += r.y;
+    if (S == 0) ik += r.y;
   }
   if (__any_sync(0xffffffffu, !isfinite(fin)) && lane == 0) atomicOr(&K.st->status, kStNonfinite);
   return true;
