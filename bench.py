@@ -512,15 +512,15 @@ def measure_stress(args, torch, dist, local_rank: int, rank: int, peak: float,
 
 
 def measure_surrogate(torch) -> dict:
-    """The surrogate network of the parameter scans: a 384-setting scan run by the FP32 ensemble (half an RF
-    period to warm up, half to average), the network trained on 320 settings by the
-    tensor-core kernels, judged on the 64 held-out settings by the plain method's profiles;
-    plus the tensor-core GEMM rate of its widest layer at batch 1024."""
+    """The surrogate network of the parameter scans: a 2000-setting scan run by the FP32
+    ensemble (2 RF periods from the load, then averages over 2 more), the network trained on
+    1800 settings by the tensor-core kernels, judged on the 200 held-out settings by the plain
+    method's profiles; plus the tensor-core rate of its forward pass at batch 1024."""
     from paper_2109_04469_gb300 import pic, surrogate as S
 
-    settings = S.sample_settings(384, seed=11)
-    X, Y, D, pic_s = S.run_scan(settings, warm_cycles=0.5, avg_cycles=0.5)
-    tr, te = np.arange(320), np.arange(320, 384)
+    settings = S.sample_settings(2000, seed=11)
+    X, Y, D, pic_s = S.run_scan(settings, warm_cycles=2.0, avg_cycles=2.0)
+    tr, te = np.arange(1800), np.arange(1800, 2000)
     sur = S.Surrogate(batch_max=512, seed=4)
     t = time.perf_counter()
     losses = sur.fit(X[tr], Y[tr], epochs=300)
@@ -556,7 +556,8 @@ def measure_surrogate(torch) -> dict:
             "final_loss": float(losses[-1]),
             "forward_1024_us": fwd_ms * 1e3,
             "forward_tflops": fwd_flop / (fwd_ms * 1e-3) / 1e12,
-            "note": "scan runs are 1 RF period from a uniform load (not converged "
+            "held_out_dx_flag_positives": int(S.pic_flags([D[i] for i in te])[:, 1].sum()),
+            "note": "scan runs are 4 RF periods from a uniform load (not converged "
                     "discharges); the network is tiny, so its kernels are launch and latency "
                     "bound, far from the tensor-core peak"}
 

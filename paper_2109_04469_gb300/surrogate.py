@@ -23,10 +23,19 @@ F_FLOOR = 1e-6  # eV^-3/2, floor of the log EEPF
 QE, ME, EPS0 = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
 
 
-def sample_settings(n: int, seed: int = 7, per_species=(8e3, 3.2e4)) -> list[dict]:
+PER_SPECIES = 16384        # superparticles per species at load, every setting
+DENSITY = (1e15, 2e16)     # m^-3, initial density range (log-uniform): W = n A L / PER_SPECIES
+W_CENTRE = np.sqrt(DENSITY[0] * DENSITY[1]) * 1e-4 * 0.025 / PER_SPECIES
+W_SPAN = np.sqrt(DENSITY[1] / DENSITY[0])
+
+
+def sample_settings(n: int, seed: int = 7) -> list[dict]:
     """n settings on a Latin hypercube over the scan ranges of the batched workload (p 1-20 Pa,
-    V 100-500 V, N_t 500-4000, 100-800 cells, R 0-0.7, gamma 0-0.4) with small populations
-    (a 4x weight range) so that a scan of many settings runs in seconds."""
+    V 100-500 V, N_t 500-4000, 100-800 cells, R 0-0.7, gamma 0-0.4) and over the weight:
+    every setting loads PER_SPECIES superparticles per species, so the weight W (a 20x range)
+    carries the initial density (1e15-2e16 m^-3), which is what makes the coarser grids of the
+    denser settings break dx <= lambda_D.  Capacity 24x the load holds the fastest-ionizing
+    settings over the scan's run length."""
     rng = np.random.default_rng(seed)
     d = 7
     u = (np.argsort(rng.random((d, n)), axis=1) + rng.random((d, n))) / n
@@ -35,17 +44,17 @@ def sample_settings(n: int, seed: int = 7, per_species=(8e3, 3.2e4)) -> list[dic
         return float(np.exp(np.log(a) + x * (np.log(b) - np.log(a))))
 
     out = []
-    gap, dens, area = 0.025, 1e15, workloads.COMMON["area_m2"]
+    gap, area = 0.025, workloads.COMMON["area_m2"]
     for i in range(n):
-        nps = int(logu(u[4, i], *per_species))
+        dens = logu(u[4, i], *DENSITY)
         out.append(dict(
             workloads.COMMON, gap_m=gap, pressure_pa=logu(u[0, i], 1.0, 20.0),
             v_rf_amp_v=100.0 + 400.0 * float(u[1, i]),
             steps_per_rf=int(round(logu(u[2, i], 500, 4000))),
-            n_cells=int(round(logu(u[3, i], 100, 800))), weight=dens * area * gap / nps,
-            refl_e=0.7 * float(u[5, i]), gamma_see=0.4 * float(u[6, i]), init_per_species=nps,
-            capacity_per_species=8 * nps + 4096, instance=i, eepf_bins=N_EEPF,
-            eepf_emax_ev=EEPF_EMAX, precision=pic.PIC_FP32))
+            n_cells=int(round(logu(u[3, i], 100, 800))), weight=dens * area * gap / PER_SPECIES,
+            refl_e=0.7 * float(u[5, i]), gamma_see=0.4 * float(u[6, i]),
+            init_per_species=PER_SPECIES, capacity_per_species=24 * PER_SPECIES + 4096,
+            instance=i, eepf_bins=N_EEPF, eepf_emax_ev=EEPF_EMAX, precision=pic.PIC_FP32))
     return out
 
 
@@ -58,7 +67,7 @@ def features(c: dict) -> np.ndarray:
         (c["v_rf_amp_v"] - 300.0) / 200.0,
         (np.log(dt) - np.log(1.0 / (13.56e6 * np.sqrt(500 * 4000)))) / np.log(np.sqrt(8.0)),
         (np.log(dx) - np.log(0.025 / np.sqrt(100 * 800))) / np.log(np.sqrt(8.0)),
-        (np.log(c["weight"]) - np.log(1e4)) / np.log(4.0),
+        (np.log(c["weight"]) - np.log(W_CENTRE)) / np.log(W_SPAN),
         c["refl_e"] / 0.35 - 1.0, c["gamma_see"] / 0.2 - 1.0], dtype=np.float32)
 
 
@@ -73,7 +82,7 @@ def targets(diag: dict, gap: float) -> np.ndarray:
                            np.log10(np.maximum(eepf, 0.0) + F_FLOOR)]).astype(np.float32)
 
 
-def run_scan(settings: list[dict], warm_cycles: float = 1.0, avg_cycles: float = 1.0,
+def run_scan(settings: list[dict], warm_cycles: float = 2.0, avg_cycles: float = 2.0,
              members: int = 128, stream=None):
     """Run every setting with the FP32 ensemble: warm_cycles RF periods, then averages over
     avg_cycles periods.  Returns (features [n, 7], targets [n, 192], PIC diagnostics list,

@@ -1,8 +1,11 @@
-"""The surrogate pipeline end to end on the GPU: a scan of settings run by the FP32 ensemble
-(the plain method), the network trained on it by the tensor-core kernels, and judged on
-held-out settings by the plain method's own profiles.  What the network gains: profiles of
-unseen settings closer than the best constant guess (the training mean), at a tiny fraction
-of the cost of running them, and the §3.5 accuracy flags of unseen settings."""
+"""The surrogate pipeline end to end on the GPU, at the scale of the learned-surrogate workload:
+a 2000-setting scan run by the FP32 ensemble (the plain method; 2 RF periods from the uniform
+load, then averages over 2 more), the network trained on 90 % of it by the tensor-core
+kernels, and judged on the 10 % held out by the plain method's own profiles.  What the network
+gains: held-out density profiles within 5 % (mean relative deviation from the PIC profile of
+the same setting) where the best constant guess (the training mean) is off by tens of per
+cent, at a tiny fraction of the cost of running the settings; and the §3.5 accuracy flags of
+unseen settings, including dx > lambda_D, which the denser settings of the scan break."""
 import time
 
 import numpy as np
@@ -10,6 +13,8 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+
+N_SETTINGS, HELD_OUT = 2000, 200
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -20,13 +25,15 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def test_surrogate_learns_the_scan_and_beats_the_mean():
+def test_surrogate_reproduces_held_out_profiles_within_five_percent():
     from paper_2109_04469_gb300 import surrogate as S
 
-    settings = S.sample_settings(384, seed=11)
-    X, Y, D, pic_s = S.run_scan(settings, warm_cycles=0.5, avg_cycles=0.5)
-    assert X.shape == (384, 7) and Y.shape == (384, 192) and np.all(np.isfinite(Y))
-    tr, te = np.arange(320), np.arange(320, 384)
+    settings = S.sample_settings(N_SETTINGS, seed=11)
+    X, Y, D, pic_s = S.run_scan(settings, warm_cycles=2.0, avg_cycles=2.0)
+    assert X.shape == (N_SETTINGS, 7) and Y.shape == (N_SETTINGS, 192) and np.all(np.isfinite(Y))
+    assert all(d["return_code"] >= 0 for d in D)  # no dropped births, no device error
+    tr = np.arange(N_SETTINGS - HELD_OUT)
+    te = np.arange(N_SETTINGS - HELD_OUT, N_SETTINGS)
     sur = S.Surrogate(batch_max=512, seed=4)
     losses = sur.fit(X[tr], Y[tr], epochs=300)
     assert losses[-1] < losses[0] / 4
@@ -35,12 +42,16 @@ def test_surrogate_learns_the_scan_and_beats_the_mean():
     net_s = time.perf_counter() - t
     err = S.profile_error(P, Y[te])
     base = S.profile_error(np.repeat(Y[tr].mean(axis=0, keepdims=True), len(te), 0), Y[te])
-    print("held-out profile error: network mean %.3f median %.3f | training mean %.3f"
-          % (err.mean(), np.median(err), base.mean()))
-    assert err.mean() < 0.8 * base.mean()
+    print("held-out profile error: network mean %.4f median %.4f p90 %.4f | training mean %.3f"
+          % (err.mean(), np.median(err), np.quantile(err, 0.9), base.mean()))
+    assert err.mean() <= 0.05
+    assert base.mean() > 5 * err.mean()
     assert net_s * len(settings) / len(te) < pic_s / 100  # per setting, >100x cheaper
     pf = S.accuracy_flags([settings[i] for i in te], P)
     gf = S.pic_flags([D[i] for i in te])
     agree = (pf == gf).mean(axis=0)
-    print("flag agreement (omega_pe dt > 0.2, dx > lambda_D):", agree)
-    assert agree[0] >= 0.75
+    print("flag agreement (omega_pe dt > 0.2, dx > lambda_D):", agree,
+          "held-out positives:", gf.sum(axis=0))
+    assert gf[:, 1].sum() >= 10 and (~gf[:, 1]).sum() >= 10  # both outcomes occur
+    assert gf[:, 0].sum() >= 10 and (~gf[:, 0]).sum() >= 10
+    assert agree[0] >= 0.95 and agree[1] >= 0.95
