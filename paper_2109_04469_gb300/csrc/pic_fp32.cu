@@ -17,11 +17,12 @@
 // counter-based generator then runs only at candidates, surfaces and births.
 //
 // Work split: every warp owns a contiguous, balanced range of each species and walks it in
-// 128-particle tiles staged in shared memory by bulk asynchronous copies (kStages - 1 tiles
-// in flight per warp), with particle p = tile + 32 k + lane (k = 0..3): ranking holes and
-// births with ballot/popc per k is already particle order, so warps never wait for one
-// another.  The hole and birth lists are per warp.  The rare branches (surfaces, collisions,
-// EEPF samples) are out-of-line calls so the hot loop stays small.
+// 128-particle tiles staged in shared memory by bulk asynchronous copies (stages - 1 tiles
+// in flight per warp); a lane holds two neighbouring particles of each 64-particle half of a
+// tile, so ballots and popcounts rank holes, births and queued work in particle order and
+// warps never wait for one another.  The hole and birth lists are per warp.  The rare work
+// (surfaces, collisions, EEPF samples) is queued and drained 32 entries at a time through
+// out-of-line calls, so the hot loop stays small.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -332,7 +333,9 @@ __device__ __forceinline__ void put_rec(float* list, size_t cap, long long slot,
 
 // A warp's staging of one 128-particle tile (bulk-copy destination; 16-byte aligned fields).
 // Only the two words every particle needs are staged; the id is read by the rare paths.
-constexpr int kStages = 2;
+// Tile stages per warp: the single run keeps two tiles in flight; the ensemble one, since a
+// third stage would take from the L1 that its members' collision tables are read through.
+constexpr int kStagesRun = 3, kStagesEns = 2;
 struct WarpTile {
   unsigned ccd[128];  // cell | countdown << 16
   float2 ov[128];     // off, vx
@@ -346,17 +349,21 @@ struct WarpTile {
 // step unless the particle left the gap, whose cell is kept as a signed 16-bit value
 // saturated at +-32767 (with at most 4096 cells a saturated cell is still outside after a
 // mirror reflection, so every surface decision is the unsaturated one's).
-struct Cand {
+struct __align__(16) Cand {  // one 16-byte shared-memory access
   unsigned pk;
   unsigned aux;
   float off, vx;
 };
 constexpr int kCandQ = 160;  // up to 31 waiting + 128 from one tile
-struct __align__(128) WarpPipe {  // one per warp, back to back in shared memory
-  WarpTile t[kStages];
-  unsigned long long bar[kStages];
+struct __align__(16) WarpRare {
   Rec32 recE[32], recI[32];  // the lanes' births of the current drain
   Cand cq[kCandQ];
+};
+template <int NS>
+struct __align__(128) WarpPipe {  // one per warp, back to back in shared memory
+  WarpTile t[NS];
+  unsigned long long bar[NS];
+  WarpRare r;
 };
 struct PipeCount {         // per-warp, warp-uniform, in registers
   unsigned issued, waited;  // tiles issued / consumed by this warp so far
@@ -380,7 +387,7 @@ __device__ __forceinline__ bool in_eepf_cells(int nc, int cell) {
 // births) listed: the caller advances hk by the first and ek (and, for electrons, ik) by the
 // second.
 template <int S>
-__device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step, WarpPipe& P,
+__device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step, WarpRare& P,
                                      int n, int nq, unsigned* sCe, unsigned* sCi,
                                      unsigned long long* sCnt, long long hk, long long ek,
                                      long long ik) {
@@ -452,11 +459,11 @@ __device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step
 
 // Lane 0 starts the bulk copies of particles [t0, t0 + n) into the next stage (t0 is a
 // multiple of 32, so every source starts on a 16-byte boundary).
-template <int S>
-__device__ __forceinline__ void issue_tile(const DevCtx& K, WarpPipe& P, PipeCount& Q,
+template <int S, int NS>
+__device__ __forceinline__ void issue_tile(const DevCtx& K, WarpPipe<NS>& P, PipeCount& Q,
                                            long long t0, int n) {
   if ((threadIdx.x & 31) == 0) {
-    const unsigned st = Q.issued % kStages;
+    const unsigned st = Q.issued % NS;
     WarpTile& T = P.t[st];
     const unsigned b4 = round16(4u * n), b8 = round16(8u * n);
     fence_proxy_async_smem();  // the lanes' earlier reads of this stage come first
@@ -489,7 +496,7 @@ __device__ __forceinline__ int tile_index(int q, int lane) {
 template <int S, bool FULL>
 __device__ __forceinline__ void tile32_body(const DevCtx& K, long long tile, int nv,
                                             const WarpTile& T, const float2* sE, unsigned* sCe,
-                                            unsigned* sCi, WarpPipe& P, int& nq, float& fin) {
+                                            unsigned* sCi, WarpRare& P, int& nq, float& fin) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int nc = K.nc;
@@ -576,32 +583,32 @@ __device__ __forceinline__ void tile32_body(const DevCtx& K, long long tile, int
 }
 
 // One warp walks particles [q, qe) of species S (q a multiple of 32) in 128-particle tiles
-// staged in shared memory by bulk copies, kStages - 1 tiles in flight.  Holes and births go
+// staged in shared memory by bulk copies, NS - 1 tiles in flight.  Holes and births go
 // to the warp's lists at hk / ek / ik (running offsets, warp-uniform).  Returns false if a
 // staged tile never arrived.
-template <int S>
+template <int S, int NS>
 __device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long long q,
                                             long long qe, const float2* sE, unsigned* sCe,
                                             unsigned* sCi, unsigned long long* sCnt,
-                                            WarpPipe& P, PipeCount& Q, long long& hk,
+                                            WarpPipe<NS>& P, PipeCount& Q, long long& hk,
                                             long long& ek, long long& ik) {
   const int lane = threadIdx.x & 31;
   const DevCtx* __restrict__ G = K.self;
   const int ntiles = (int)((qe - q + 127) / 128);
   int nq = 0;          // queued entries (warp-uniform)
   float fin = 0.0f;    // stays finite unless a velocity was not: v * 0 + fin
-  for (int t = 0; t < kStages - 1 && t < ntiles; ++t)
+  for (int t = 0; t < NS - 1 && t < ntiles; ++t)
     issue_tile<S>(K, P, Q, q + 128 * t, (int)min(128ll, qe - q - 128ll * t));
   for (int t = 0; t < ntiles; ++t) {
-    if (t + kStages - 1 < ntiles) {
-      const int u = t + kStages - 1;
+    if (t + NS - 1 < ntiles) {
+      const int u = t + NS - 1;
       issue_tile<S>(K, P, Q, q + 128ll * u, (int)min(128ll, qe - q - 128ll * u));
     }
-    const unsigned st = Q.waited % kStages;
-    if (!mbar_wait(&P.bar[st], (Q.waited / kStages) & 1u)) {
+    const unsigned st = Q.waited % NS;
+    if (!mbar_wait(&P.bar[st], (Q.waited / NS) & 1u)) {
       atomicOr(&K.st->status, kStTimeout);
       for (unsigned w = Q.waited + 1; w < Q.issued; ++w)  // let the copies in flight land
-        (void)mbar_wait(&P.bar[w % kStages], (w / kStages) & 1u);
+        (void)mbar_wait(&P.bar[w % NS], (w / NS) & 1u);
       Q.waited = Q.issued;
       return false;
     }
@@ -609,11 +616,11 @@ __device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long
     const long long tile = q + 128ll * t;
     const int nv = (int)min(128ll, qe - tile);  // particles of this tile
     if (nv == 128)
-      tile32_body<S, true>(K, tile, 128, P.t[st], sE, sCe, sCi, P, nq, fin);
+      tile32_body<S, true>(K, tile, 128, P.t[st], sE, sCe, sCi, P.r, nq, fin);
     else
-      tile32_body<S, false>(K, tile, nv, P.t[st], sE, sCe, sCi, P, nq, fin);
+      tile32_body<S, false>(K, tile, nv, P.t[st], sE, sCe, sCi, P.r, nq, fin);
     while (nq >= 32) {  // the rare work, 32 entries at a time, in queue order
-      const int2 r = drain32<S>(G, step, P, 32, nq, sCe, sCi, sCnt, hk, ek, ik);
+      const int2 r = drain32<S>(G, step, P.r, 32, nq, sCe, sCi, sCnt, hk, ek, ik);
       hk += r.x;
       ek += r.y;
       if (S == 0) ik += r.y;
@@ -622,7 +629,7 @@ __device__ __forceinline__ bool warp_pass32(const DevCtx& K, unsigned step, long
     __syncwarp();  // every lane is done with this stage before it is refilled
   }
   if (nq > 0) {
-    const int2 r = drain32<S>(G, step, P, nq, nq, sCe, sCi, sCnt, hk, ek, ik);
+    const int2 r = drain32<S>(G, step, P.r, nq, nq, sCe, sCi, sCnt, hk, ek, ik);
     hk += r.x;
     ek += r.y;
     if (S == 0) ik += r.y;
@@ -643,6 +650,14 @@ __device__ __forceinline__ void flush32(const DevCtx& K, unsigned* sC, unsigned 
   __syncthreads();
 }
 
+// The longest range a warp of the grid gets out of n particles: range_begin floors
+// units g / GW, so no range exceeds ceil(units / GW) units of kUnit particles.
+__device__ __forceinline__ long long warp_range_max(long long n) {
+  const long long GW = (long long)gridDim.x * kWarps32;
+  const long long units = (n + kUnit - 1) / kUnit;
+  return (units + GW - 1) / GW * kUnit;
+}
+
 // Species S for the whole block: each warp its own range, in rounds that bound the 32-bit
 // counters.  The warp's list lengths go to wc[list][warp] (lists: 0, 1 holes of electrons /
 // ions; 2, 3 electron births from electron / ion ranges; 4 ion births), its first particle of
@@ -651,16 +666,15 @@ template <int S>
 __device__ __forceinline__ void block_pass32(const DevCtx& K, unsigned step, long long n,
                                              const float2* sE, unsigned* sC,
                                              unsigned long long* sCnt, unsigned long long* Cn,
-                                             WarpPipe& P, PipeCount& Q, int (*wc)[kWarps32],
+                                             WarpPipe<kStagesRun>& P, PipeCount& Q,
+                                             int (*wc)[kWarps32],
                                              long long (*wb)[kWarps32]) {
-  const int GW = gridDim.x * kWarps32;  // warps of the grid
   const int gw = blockIdx.x * kWarps32 + (threadIdx.x >> 5);
   const long long q0 = range_begin_d(n, gw, K.gw_div), q1 = range_begin_d(n, gw + 1, K.gw_div);
   long long hk = q0, ek = q0, ik = q0;  // list slots of this warp
-  // rounds: uniform across the grid; no warp range exceeds ceil(units / GW) units of 32
-  // particles (range_begin floors units g / GW), and an empty round only costs a flush
-  const long long units = (n + kUnit - 1) / kUnit;
-  const long long wmax = (units + GW - 1) / GW * kUnit;
+  // rounds: uniform across the grid (every warp's range is within warp_range_max), and an
+  // empty round only costs a flush
+  const long long wmax = warp_range_max(n);
   const int rounds = (int)((wmax + kRoundPerWarp - 1) / kRoundPerWarp);
   bool ok = true;
   for (int r = 0; r < rounds; ++r) {
@@ -811,11 +825,12 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
   const int nx = K.nx;
   float2* sE = reinterpret_cast<float2*>(smem32);           // [2][nx] kick, kick difference
   unsigned* sC = reinterpret_cast<unsigned*>(sE + 2 * nx);  // [2][nx] 32-bit counts
-  WarpPipe& P = reinterpret_cast<WarpPipe*>(smem32 + pipes_offset(nx))[threadIdx.x >> 5];
+  WarpPipe<kStagesRun>& P =
+      reinterpret_cast<WarpPipe<kStagesRun>*>(smem32 + pipes_offset(nx))[threadIdx.x >> 5];
   __shared__ unsigned long long sCnt[kNumCounters];
   chain_release();  // the placement launch may take the SM room this pass leaves
   if ((threadIdx.x & 31) == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&P.bar[s], 1u);
+    for (int s = 0; s < kStagesRun; ++s) mbar_init(&P.bar[s], 1u);
     fence_mbar_init();
   }
   PipeCount Q{0u, 0u};
@@ -836,7 +851,9 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
   __shared__ int wc[5][kWarps32];
   __shared__ long long wb[2][kWarps32];
   block_pass32<0>(K, step, ne, sE, sC, sCnt, Cn, P, Q, wc, wb);
-  flush32(K, sC, Cn);
+  // when every warp's electron and ion ranges together fit one round, the counters stay in
+  // range across both passes and each warp goes on to its ions without waiting for the block
+  if (warp_range_max(ne) + warp_range_max(ni) > kRoundPerWarp) flush32(K, sC, Cn);
   block_pass32<1>(K, step, ni, sE + nx, sC, sCnt, Cn, P, Q, wc, wb);
   flush32(K, sC, Cn);  // ends with a block barrier: every warp's lists are complete
   if (threadIdx.x < kNumCounters && sCnt[threadIdx.x])
@@ -1129,9 +1146,10 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
     const unsigned TC = (unsigned)sC0[n];
     PipeCount Q{0u, 0u};
     bool ok = true;
-    WarpPipe& P = reinterpret_cast<WarpPipe*>(esm + (size_t)E->pipes_off)[warp];
+    WarpPipe<kStagesEns>& P =
+        reinterpret_cast<WarpPipe<kStagesEns>*>(esm + (size_t)E->pipes_off)[warp];
     if (lane == 0) {
-      for (int k = 0; k < kStages; ++k) mbar_init(&P.bar[k], 1u);
+      for (int k = 0; k < kStagesEns; ++k) mbar_init(&P.bar[k], 1u);
       fence_mbar_init();
     }
     int cur = -1;  // member (position in the order) whose tables are in shared memory
@@ -1210,7 +1228,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
       atomicAdd(&E->sims[sOrd[cur]]->counters[threadIdx.x], sCnt[threadIdx.x]);
     __syncwarp();
     if (lane == 0)
-      for (int k = 0; k < kStages; ++k) mbar_inval(&P.bar[k]);
+      for (int k = 0; k < kStagesEns; ++k) mbar_inval(&P.bar[k]);
   }
   if (!grid_barrier(E)) return;
   ensemble_phase2(E, par, sEstep, n, sNe, sNi, sIt, sG, esm, sT);
@@ -1237,7 +1255,9 @@ cudaError_t launch_selftest_waits(EnsDev* E, int* status, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------ launchers
-size_t push32_smem_bytes(int nx) { return pipes_offset(nx) + sizeof(WarpPipe) * kWarps32; }
+size_t push32_smem_bytes(int nx) {
+  return pipes_offset(nx) + sizeof(WarpPipe<kStagesRun>) * kWarps32;
+}
 
 cudaError_t launch_push_fp32(const DevCtx& K, int grid, cudaStream_t s) {
   return launch_chained(k_push_fp32, (unsigned)grid, (unsigned)kBlock, push32_smem_bytes(K.nx),
@@ -1251,7 +1271,7 @@ cudaError_t launch_place_fp32(const DevCtx& K, int grid, cudaStream_t s) {
 
 size_t ensemble_pipes_offset(int nx_max) { return pipes_offset(nx_max); }
 size_t ensemble_smem_bytes(int nx_max, int gcap_max) {
-  const size_t p1 = pipes_offset(nx_max) + sizeof(WarpPipe) * kWarps32;
+  const size_t p1 = pipes_offset(nx_max) + sizeof(WarpPipe<kStagesEns>) * kWarps32;
   const size_t p2 = place_smem_bytes(nx_max, gcap_max);
   return p1 > p2 ? p1 : p2;
 }
