@@ -152,15 +152,18 @@ struct SurfOut {  // state after step 5; flags: bit 0 removed, bit 1 electron em
   int cell;
   float off, vx;
   int flags;
+  unsigned ev;  // events: bit k adds one to event counter k
 };
 
 // Step 5 for a particle that left the gap (x <= 0 or x >= L).  An emitted electron is
-// written to *em (this lane's slot in shared memory).
+// written to *em (this lane's slot in shared memory).  The events it counts are returned as
+// bits, for the drain to add up over the warp.
 template <int S>
 __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned step, long long p,
                                           int cell, float off, float vx, bool left,
-                                          unsigned* sCe, unsigned long long* sCnt, Rec32* em) {
+                                          unsigned* sCe, Rec32* em) {
   const int nc = G->nc;
+  unsigned ev = 0u;
   const unsigned pid = G->id[S][p];
   const float vy = G->fvy[S][p], vz = G->fvz[S][p];  // in flight during the draw below
   // the per-step block of the FP64 contract: its third word decides the surface event
@@ -177,15 +180,16 @@ __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned
       }
       renorm(cell, off);
       vx = -vx;
-      atomicAdd(&sCnt[kCnERefl], 1ull);
-      if (!(cell < 0 || (cell == 0 && off == 0.0f) || cell >= nc)) return SurfOut{cell, off, vx, 0};
+      ev |= 1u << kCnERefl;
+      if (!(cell < 0 || (cell == 0 && off == 0.0f) || cell >= nc))
+        return SurfOut{cell, off, vx, 0, ev};
     }
-    atomicAdd(&sCnt[left ? kCnEAbsL : kCnEAbsR], 1ull);
+    ev |= 1u << (left ? kCnEAbsL : kCnEAbsR);
     const float t = (vx * vx + vy * vy + vz * vz) * G->f_emfac_e * G->f_fedf_inv_de;
     if (t < (float)G->fedf_bins) atomicAdd(&G->fedf[(int)t], 1ull);
-    return SurfOut{cell, off, vx, 1};
+    return SurfOut{cell, off, vx, 1, ev};
   }
-  atomicAdd(&sCnt[left ? kCnIAbsL : kCnIAbsR], 1ull);
+  ev |= 1u << (left ? kCnIAbsL : kCnIAbsR);
   const float t = (vx * vx + vy * vy + vz * vz) * G->f_emfac_ilab * G->f_fedf_inv_de;
   if (t < (float)G->fedf_bins) atomicAdd(&G->fedf[G->fedf_bins + (int)t], 1ull);
   int flags = 1;
@@ -204,25 +208,25 @@ __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned
     *em = r;
     flags |= 2;
     deposit32(sCe, r.cell, r.off);
-    atomicAdd(&sCnt[kCnSee], 1ull);
+    ev |= 1u << kCnSee;
   }
-  return SurfOut{cell, off, vx, flags};
+  return SurfOut{cell, off, vx, flags, ev};
 }
 
 struct CollOut {  // state after step 6; born: an ionization pair was written
   float vx;
   unsigned cd;
   int born;
+  unsigned ev;  // events: bit k adds one to event counter k
 };
 
 // Countdown expiry: a null-collision candidate unless the flag is set (readings C-7..C-10,
 // C-13), then the next countdown.  An ionization writes the pair to *re / *ri (this lane's
-// slots in shared memory).
+// slots in shared memory).  The events it counts are returned as bits.
 template <int S>
 __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned step, long long p,
                                           int cell, float off, float vx, unsigned cd,
-                                          unsigned* sCe, unsigned* sCi, unsigned long long* sCnt,
-                                          Rec32* re, Rec32* ri) {
+                                          unsigned* sCe, unsigned* sCi, Rec32* re, Rec32* ri) {
   const unsigned pid = G->id[S][p];  // one round trip with vy, vz
   float vy = G->fvy[S][p], vz = G->fvz[S][p];  // in flight during the draws below
   Stream sc(*G, S, kPurColl, pid, step);
@@ -230,12 +234,13 @@ __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned
   ++sc.block;
   const bool candidate = !(cd & kCdFlag);
   const unsigned cd_next = draw_countdown(u24(wp.b), G->f_lnq[S]);
-  if (!candidate) return CollOut{vx, cd_next, 0};
+  if (!candidate) return CollOut{vx, cd_next, 0, 0u};
+  unsigned ev = 0u;
   bool dirty = false;
   int born = 0;
   const float up = u24(wp.a);
   if (S == 0) {
-    atomicAdd(&sCnt[kCnECand], 1ull);
+    ev |= 1u << kCnECand;
     const float v2 = vx * vx + vy * vy + vz * vz;
     const float eps = v2 * G->f_emfac_e;
     float F0, F1, F2;
@@ -248,7 +253,7 @@ __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned
       const float sp = vmag * sqrtf(1.0f - G->f_mr2 * (1.0f - cosx));
       vx = n0 * sp; vy = n1 * sp; vz = n2 * sp;
       dirty = true;
-      atomicAdd(&sCnt[kCnEEla], 1ull);
+      ev |= 1u << kCnEEla;
     } else if (up < F1) {  // excitation
       if (eps >= (float)kEExc) {
         float n0, n1, n2;
@@ -256,7 +261,7 @@ __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned
         const float sp = sqrtf((eps - (float)kEExc) * G->f_spd2_e);
         vx = n0 * sp; vy = n1 * sp; vz = n2 * sp;
         dirty = true;
-        atomicAdd(&sCnt[kCnEExc], 1ull);
+        ev |= 1u << kCnEExc;
       }
     } else if (up < F2) {  // ionization (C-10)
       if (eps >= (float)kEIon) {
@@ -274,11 +279,11 @@ __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned
         born = 1;
         deposit32(sCe, cell, off);
         deposit32(sCi, cell, off);
-        atomicAdd(&sCnt[kCnEIon], 1ull);
+        ev |= 1u << kCnEIon;
       }
     }
   } else {
-    atomicAdd(&sCnt[kCnICand], 1ull);
+    ev |= 1u << kCnICand;
     float g0, g1, g2, g3;
     gauss_pair_f(sc, g0, g1);
     gauss_pair_f(sc, g2, g3);
@@ -295,31 +300,32 @@ __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned
       vy = 0.5f * (vy + n1) + d1 * hg;
       vz = 0.5f * (vz + n2) + d2 * hg;
       dirty = true;
-      atomicAdd(&sCnt[kCnIIso], 1ull);
+      ev |= 1u << kCnIIso;
     } else if (up < F1) {  // charge transfer
       vx = n0; vy = n1; vz = n2;
       dirty = true;
-      atomicAdd(&sCnt[kCnICx], 1ull);
+      ev |= 1u << kCnICx;
     }
   }
   if (dirty) {
     G->fvy[S][p] = vy;
     G->fvz[S][p] = vz;
   }
-  return CollOut{vx, cd_next, born};
+  return CollOut{vx, cd_next, born, ev};
 }
 
-// EEPF sample of an electron in the centre window (reading C-18).
-__device__ __noinline__ void eepf32(const DevCtx* __restrict__ G, long long p, int cell,
-                                    float off, float vx, unsigned long long* sCnt) {
+// EEPF sample of an electron in the centre window (reading C-18).  Returns the sample's
+// energy in units of 2^-20 eV (rounded from FP32), or exactly -1 if the electron is outside
+// the window.
+__device__ __noinline__ long long eepf32(const DevCtx* __restrict__ G, long long p, int cell,
+                                         float off, float vx) {
   const float d = ((float)cell - 0.5f * (float)G->nc) + off;
-  if (!(d > -0.5f && d < 0.5f)) return;
+  if (!(d > -0.5f && d < 0.5f)) return -1ll;
   const float vy = G->fvy[0][p], vz = G->fvz[0][p];
   const float eps = (vx * vx + vy * vy + vz * vz) * G->f_emfac_e;
   if (eps * G->f_eepf_inv_de < (float)G->eepf_bins)
     atomicAdd(&G->eepf[(int)(eps * G->f_eepf_inv_de)], 1ull);
-  atomicAdd(&sCnt[kCnEepfN], 1ull);
-  atomicAdd(&sCnt[kCnEepfEsum], (unsigned long long)__float2ll_rn(eps * 1048576.0f));
+  return __float2ll_rn(eps * 1048576.0f);
 }
 
 __device__ __forceinline__ void put_rec(float* list, size_t cap, long long slot, const Rec32& r) {
@@ -396,6 +402,7 @@ __device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step
   const unsigned lt = (1u << lane) - 1u;
   bool dead = false, born = false;
   long long p = 0;
+  unsigned ev = 0u;  // this lane's events, bit k for event counter k
   if (lane < n) {
     const Cand c = P.cq[lane];
     p = (long long)(c.pk & 0x7FFFFFFFu);
@@ -406,7 +413,8 @@ __device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step
     if (c.pk >> 31) {  // step 5: left the gap
       cell = (int)(short)(c.aux & 0xFFFFu);
       const bool left = cell < 0 || (cell == 0 && off == 0.0f);
-      const SurfOut r = surface32<S>(G, step, p, cell, off, vx, left, sCe, sCnt, &P.recE[lane]);
+      const SurfOut r = surface32<S>(G, step, p, cell, off, vx, left, sCe, &P.recE[lane]);
+      ev |= r.ev;
       cell = r.cell;
       off = r.off;
       vx = r.vx;
@@ -421,8 +429,9 @@ __device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step
     }
     if (!dead) {
       if ((cd & 0x7FFFu) == 0u) {  // the countdown ran out: step 6
-        const CollOut o = collide32<S>(G, step, p, cell, off, vx, cd, sCe, sCi, sCnt,
-                                       &P.recE[lane], &P.recI[lane]);
+        const CollOut o =
+            collide32<S>(G, step, p, cell, off, vx, cd, sCe, sCi, &P.recE[lane], &P.recI[lane]);
+        ev |= o.ev;
         vx = o.vx;
         cd = o.cd;
         born = born || o.born != 0;  // an ionization pair (electrons only)
@@ -432,8 +441,22 @@ __device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step
         G->ov[S][p] = make_float2(off, vx);
         G->ccd[S][p] = ((unsigned)cell & 0xFFFFu) | (cd << 16);
       }
-      if (S == 0 && in_eepf_cells(G->nc, cell)) eepf32(G, p, cell, off, vx, sCnt);
+      if (S == 0 && in_eepf_cells(G->nc, cell)) {
+        const long long e = eepf32(G, p, cell, off, vx);
+        if (e != -1ll) {  // rare: one lane of a few, so the 64-bit sum is added directly
+          ev |= 1u << kCnEepfN;
+          atomicAdd(&sCnt[kCnEepfEsum], (unsigned long long)e);
+        }
+      }
     }
+  }
+  // the drain's events into the block's counters: one shared atomic per counter that
+  // occurred (lanes adding one by one would all hit the same address)
+  const unsigned evs = __reduce_or_sync(0xffffffffu, ev);
+  for (unsigned b = evs; b != 0u; b &= b - 1u) {
+    const int k = __ffs(b) - 1;
+    const unsigned m = __ballot_sync(0xffffffffu, (ev >> k) & 1u);
+    if (lane == 0) atomicAdd(&sCnt[k], (unsigned long long)__popc(m));
   }
   const unsigned mh = __ballot_sync(0xffffffffu, dead);
   const unsigned mb = __ballot_sync(0xffffffffu, born);
