@@ -149,7 +149,9 @@ int pic_workspace_bytes(const pic_params* p, size_t* bytes);
 /* Create a simulation in the caller's workspace on cuda_stream (a cudaStream_t, or NULL
  * for the legacy default stream): derives the constants of §2, builds the collision tables
  * (reading C-XS) and drive table on the host, loads the initial uniform Maxwellian
- * population (reading C-22) and deposits it.  Synchronises the stream before returning. */
+ * population (reading C-22) and deposits it.  Besides the handle it allocates one small
+ * pinned host buffer (a few tens of KB: pic_diag's read-back), freed by pic_free; device
+ * memory is the caller's workspace only.  Synchronises the stream before returning. */
 int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void* cuda_stream,
              pic_handle** out);
 
@@ -167,9 +169,11 @@ int pic_sync(pic_handle* h);
  * step running beside it in the same launch).  Same results as pic_step. */
 int pic_step_profiled(pic_handle* h, int64_t n_steps, double* ms_out);
 
-/* Synchronise and reduce the accumulators into physical diagnostics (host side).  Returns
- * the sticky device status if it is an error, else PIC_WARN_UNSTABLE when the run is
- * numerically unstable (see PIC_WARN_UNSTABLE; §3.5 names such runs), else PIC_OK. */
+/* Reduce the accumulators into physical diagnostics (host side).  The electrons' max |vx|
+ * and sum of |v|^2 are reduced on the device and everything is read back into the handle's
+ * pinned buffer with one stream synchronization.  Returns the sticky device status if it is
+ * an error, else PIC_WARN_UNSTABLE when the run is numerically unstable (see
+ * PIC_WARN_UNSTABLE; §3.5 names such runs), else PIC_OK. */
 int pic_diag(pic_handle* h, pic_diag_out* out);
 
 /* Copy one species' particles to host arrays of length >= capacity; *n_out = count.
@@ -178,7 +182,10 @@ int pic_get_particles(pic_handle* h, int species, double* x, double* vx, double*
                       double* vz, uint32_t* id, int64_t capacity, int64_t* n_out);
 
 /* Replace one species' particles from host arrays of length n and set its id counter,
- * then redeposit its charge (§2 step 1).  Synchronises. */
+ * then redeposit its charge (§2 step 1).  An FP32 handle reads arrays in pinned or
+ * registered host memory directly from its conversion kernel (over the host link, no device
+ * copy of the FP64 values); other arrays, and every array of an FP64 handle, are copied to
+ * the device first.  Synchronises once, after which the host arrays may be reused. */
 int pic_set_particles(pic_handle* h, int species, const double* x, const double* vx,
                       const double* vy, const double* vz, const uint32_t* id, int64_t n,
                       uint32_t next_id);
@@ -233,7 +240,8 @@ int pic_get_derived(pic_handle* h, double* out);
  * legacy default stream), 8 blocks per SM.  Synchronises. */
 int pic_fp64_rate(void* cuda_stream, double* rates);
 
-/* Release the handle (host memory only; the caller frees the workspace afterwards). */
+/* Release the handle and its pinned read-back buffer (host memory only; the caller frees
+ * the workspace afterwards). */
 void pic_free(pic_handle* h);
 
 /* Static string for a return code. */

@@ -254,7 +254,47 @@ struct pic_handle {
   int push_grid;
   int place_grid;
   int last_status;
+  // pinned host staging of pic_diag's read-back (state, counters, averages, distributions),
+  // written by the diagnostics launch through its device mapping (stage_dev)
+  char* stage = nullptr;
+  char* stage_dev = nullptr;
+  ~pic_handle() {
+    if (stage) cudaFreeHost(stage);
+  }
 };
+
+namespace {
+// If *p is host memory the device can address (pinned or registered), replace it by its
+// device address and return true; false for other memory (then it is copied instead).
+template <class T>
+bool device_view(const T** p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, *p) != cudaSuccess) {
+    (void)cudaGetLastError();  // not a CUDA-known pointer: not an error of this call
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return false;
+  *p = static_cast<const T*>(a.devicePointer);
+  return true;
+}
+
+// Byte offsets of pic_diag's read-back in the pinned staging buffer.
+struct StageLayout {
+  size_t state, counters, acc, eepf, fedf, bytes;
+};
+StageLayout stage_layout(const pic_params& p) {
+  StageLayout L;
+  auto up = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const size_t nx = (size_t)p.n_cells + 1;
+  L.state = 0;
+  L.counters = up(sizeof(DevState));
+  L.acc = L.counters + up(sizeof(uint64_t) * kNumCounters);
+  L.eepf = L.acc + up(sizeof(double) * 2 * nx);
+  L.fedf = L.eepf + up(sizeof(uint64_t) * (size_t)p.eepf_bins);
+  L.bytes = L.fedf + up(sizeof(uint64_t) * 2 * (size_t)p.fedf_bins);
+  return L;
+}
+}  // namespace
 
 namespace {
 bool is_fp32(const pic_handle* h) { return h->p.precision == PIC_FP32; }
@@ -411,7 +451,10 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   };
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      configure_kernels(nx) != cudaSuccess || (fp32 && configure_kernels32(nx) != cudaSuccess))
+      configure_kernels(nx) != cudaSuccess || (fp32 && configure_kernels32(nx) != cudaSuccess) ||
+      cudaMallocHost(reinterpret_cast<void**>(&h->stage), stage_layout(*p).bytes) != cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->stage_dev), h->stage, 0) !=
+          cudaSuccess)
     return fail(PIC_ERR_CUDA);
   // persistent particle grid: resident blocks on all SMs, fewer for small populations
   const int bps = fp32 ? push_fp32_blocks_per_sm(nx) : push_fp64_blocks_per_sm(nx);
@@ -454,10 +497,10 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
                                cudaMemcpyHostToDevice, st) != cudaSuccess))
     return fail(PIC_ERR_CUDA);
   for (int s = 0; s < 2; ++s) {
-    // the FP32 state is the FP64 load rounded, so both precisions start from one sample
+    // the FP32 state is the FP64 load rounded, so both precisions start from one sample (the
+    // FP32 conversion deposits the charge as it goes)
     if (launch_init_load(K, s, p->init_per_species, st) != cudaSuccess ||
-        (fp32 ? (launch_convert(K, s, p->init_per_species, true, st) != cudaSuccess ||
-                 launch_deposit32(K, s, 0, p->init_per_species, st) != cudaSuccess)
+        (fp32 ? launch_convert(K, s, p->init_per_species, true, st) != cudaSuccess
               : launch_deposit(K, s, 0, p->init_per_species, st) != cudaSuccess))
       return fail(PIC_ERR_CUDA);
   }
@@ -581,28 +624,33 @@ int pic_set_particles(pic_handle* h, int species, const double* x, const double*
   if (n > 0 && (!x || !vx || !vy || !vz || !id)) return PIC_ERR_PARAM;
   const DevCtx& K = h->K;
   cudaStream_t st = h->stream;
-  DevState s;
-  PIC_CUDA(cudaStreamSynchronize(st));
-  PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
-  if (n > 0) {
+  // An FP32 handle reads host arrays the device can address (pinned or registered memory)
+  // straight from its conversion kernel; otherwise they are copied into the FP64 buffers
+  // first.  Either way the state, the counts and the charge are then set on the device, in
+  // stream order, and one synchronization returns the host arrays to the caller.
+  const double* dx_ = x;
+  const double* dvx = vx;
+  const double* dvy = vy;
+  const double* dvz = vz;
+  const uint32_t* did = id;
+  const bool direct = is_fp32(h) && n > 0 && device_view(&dx_) && device_view(&dvx) &&
+                      device_view(&dvy) && device_view(&dvz) && device_view(&did);
+  if (n > 0 && !direct) {
     PIC_CUDA(cudaMemcpyAsync(K.x[species], x, n * sizeof(double), cudaMemcpyHostToDevice, st));
     PIC_CUDA(cudaMemcpyAsync(K.vx[species], vx, n * sizeof(double), cudaMemcpyHostToDevice, st));
     PIC_CUDA(cudaMemcpyAsync(K.vy[species], vy, n * sizeof(double), cudaMemcpyHostToDevice, st));
     PIC_CUDA(cudaMemcpyAsync(K.vz[species], vz, n * sizeof(double), cudaMemcpyHostToDevice, st));
     PIC_CUDA(cudaMemcpyAsync(K.id[species], id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
   }
-  s.n[species] = n;
-  s.n_snap[species] = n;
-  s.next_id[species] = next_id;
-  PIC_CUDA(cudaMemcpyAsync(K.st, &s, sizeof s, cudaMemcpyHostToDevice, st));
-  const int buf = s.step & 1;
-  PIC_CUDA(cudaMemsetAsync(K.C + (size_t)(buf * 2 + species) * K.nx, 0,
-                           sizeof(unsigned long long) * K.nx, st));
+  PIC_CUDA(launch_set_counts(K, species, n, next_id, st));
   if (is_fp32(h)) {
-    PIC_CUDA(launch_convert(K, species, n, true, st));
-    PIC_CUDA(launch_deposit32(K, species, buf, n, st));
+    // the conversion deposits the charge as it goes
+    if (direct)
+      PIC_CUDA(launch_convert_from(K, species, n, dx_, dvx, dvy, dvz, did, st));
+    else
+      PIC_CUDA(launch_convert(K, species, n, true, st));
   } else {
-    PIC_CUDA(launch_deposit(K, species, buf, n, st));
+    PIC_CUDA(launch_deposit(K, species, -1, n, st));
   }
   PIC_CUDA(launch_field(K, st));
   PIC_CUDA(cudaStreamSynchronize(st));
@@ -707,32 +755,26 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   if ((out->eepf || out->eepf_energy) && out->eepf_bins != p.eepf_bins) return PIC_ERR_PARAM;
   if ((out->fedf_e || out->fedf_i || out->fedf_energy) && out->fedf_bins != p.fedf_bins)
     return PIC_ERR_PARAM;
-  const int rc = pic_sync(h);
-  if (rc == PIC_ERR_CUDA) return rc;
-  std::vector<double> acc((size_t)2 * nx);
-  std::vector<uint64_t> eepf(p.eepf_bins), fedf((size_t)2 * p.fedf_bins);
+  // one launch and one synchronization: the electrons' max |vx| and sum of |v|^2 reduced on
+  // the device (FP32 handles straight from the FP32 state, in cells per step), after which
+  // its last block writes the state, counters, averages and distributions into the pinned
+  // staging buffer
+  cudaStream_t st = h->stream;
+  const StageLayout L = stage_layout(p);
+  char* hs = h->stage;
+  PIC_CUDA(launch_diag(K, is_fp32(h), h->stage_dev,
+                       DiagOffsets{L.state, L.counters, L.acc, L.eepf, L.fedf}, st));
+  PIC_CUDA(cudaStreamSynchronize(st));
   DevState s;
-  PIC_CUDA(cudaMemcpy(acc.data(), K.acc, sizeof(double) * 2 * nx, cudaMemcpyDeviceToHost));
-  PIC_CUDA(cudaMemcpy(eepf.data(), K.eepf, sizeof(uint64_t) * eepf.size(), cudaMemcpyDeviceToHost));
-  PIC_CUDA(cudaMemcpy(fedf.data(), K.fedf, sizeof(uint64_t) * fedf.size(), cudaMemcpyDeviceToHost));
-  PIC_CUDA(cudaMemcpy(out->counters, K.counters, sizeof(uint64_t) * kNumCounters, cudaMemcpyDeviceToHost));
-  PIC_CUDA(cudaMemcpy(&s, K.st, sizeof s, cudaMemcpyDeviceToHost));
-  // max |vx| over the electrons for the CFL number, and their sum of |v|^2 for the mean
-  // energy of the runaway check
-  PIC_CUDA(cudaMemsetAsync(&K.st->vmax_bits, 0, sizeof(unsigned long long), h->stream));
-  PIC_CUDA(cudaMemsetAsync(&K.st->v2sum, 0, sizeof(double), h->stream));
-  if (is_fp32(h)) {  // straight from the FP32 state, in cells per step
-    PIC_CUDA(launch_max_abs_vx32(K, 0, s.n[0], &K.st->vmax_bits, h->stream));
-    PIC_CUDA(launch_sum_v2_32(K, 0, s.n[0], &K.st->v2sum, h->stream));
-  } else {
-    PIC_CUDA(launch_max_abs(K.vx[0], s.n[0], &K.st->vmax_bits, h->stream));
-    PIC_CUDA(launch_sum_v2(K, 0, s.n[0], &K.st->v2sum, h->stream));
-  }
-  unsigned long long vbits = 0;
-  double v2sum = 0.0;
-  PIC_CUDA(cudaStreamSynchronize(h->stream));
-  PIC_CUDA(cudaMemcpy(&vbits, &K.st->vmax_bits, sizeof vbits, cudaMemcpyDeviceToHost));
-  PIC_CUDA(cudaMemcpy(&v2sum, &K.st->v2sum, sizeof v2sum, cudaMemcpyDeviceToHost));
+  std::memcpy(&s, hs + L.state, sizeof s);
+  const int rc = status_code(s.status);
+  h->last_status = rc;
+  std::memcpy(out->counters, hs + L.counters, sizeof(uint64_t) * kNumCounters);
+  const double* acc = reinterpret_cast<const double*>(hs + L.acc);
+  const uint64_t* eepf = reinterpret_cast<const uint64_t*>(hs + L.eepf);
+  const uint64_t* fedf = reinterpret_cast<const uint64_t*>(hs + L.fedf);
+  const unsigned long long vbits = s.vmax_bits;
+  double v2sum = s.v2sum;
   double vmax;
   if (is_fp32(h)) {
     float f;
@@ -763,7 +805,7 @@ int pic_diag(pic_handle* h, pic_diag_out* out) {
   // EEPF with sum sqrt(e) f de = 1 (§3.1)
   const double de = p.eepf_emax_ev / p.eepf_bins;
   double tot = 0.0;
-  for (uint64_t v : eepf) tot += (double)v;
+  for (int b = 0; b < p.eepf_bins; ++b) tot += (double)eepf[b];
   for (int b = 0; b < p.eepf_bins; ++b) {
     const double ec = (b + 0.5) * de;
     if (out->eepf_energy) out->eepf_energy[b] = ec;

@@ -107,6 +107,7 @@ struct DevState {
   unsigned long long vmax_bits;  // scratch of the |vx| maximum reduction
   double v2sum;                  // scratch of the electrons' sum of |v|^2 (diagnostics)
   unsigned id_snap[2];           // next_id at the start of the current step's particle pass
+  unsigned diag_ticket;          // blocks of the diagnostics launch done (zero between calls)
 };
 
 // Device-side state of an ensemble of FP32 simulations advanced by one launch per step (the

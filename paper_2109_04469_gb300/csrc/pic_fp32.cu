@@ -913,55 +913,119 @@ struct Fp32Moves {
   }
 };
 
-// FP64 SI state (x, v) -> FP32 cell units, for the initial load and pic_set_particles; draws
-// each particle's countdown from its own stream at the current step.
-__global__ void k_to_fp32(DevCtx K, int s, long long n) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const double xn = K.x[s][q] * K.inv_dx;
-  long long j = __double2ll_rd(xn);
-  if (j > K.nc - 1) j = K.nc - 1;
-  if (j < 0) j = 0;
+// FP64 SI state (x, v) -> FP32 cell units of particles [0, n) of species s, for the initial
+// load and pic_set_particles, with their charge deposited in the same pass (16-bit weights of
+// the stored offset into block-private 64-bit counts, one global atomic per touched node and
+// block, into the current step's buffer, which the caller has cleared); draws each particle's
+// countdown from its own stream at the current step.  The SI arrays x, vx, vy, vz, id are the
+// FP64 buffers or device-readable host memory; ids read from elsewhere are stored into the
+// species' id array.
+__global__ void k_to_fp32(DevCtx K, int s, long long n, const double* __restrict__ x,
+                          const double* __restrict__ vx, const double* __restrict__ vy,
+                          const double* __restrict__ vz, const unsigned* __restrict__ id) {
+  extern __shared__ unsigned long long csm[];
+  const int nx = K.nx;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) csm[j] = 0ull;
+  __syncthreads();
+  const unsigned step = K.st->step;
   const double sc = K.dt * K.inv_dx;  // m/s -> cells per step
-  K.ov[s][q] = make_float2((float)(xn - (double)j), (float)(K.vx[s][q] * sc));
-  K.fvy[s][q] = (float)(K.vy[s][q] * sc);
-  K.fvz[s][q] = (float)(K.vz[s][q] * sc);
-  Stream st(K, s, kPurCount, K.id[s][q], K.st->step);
-  K.ccd[s][q] = (unsigned)j | ((unsigned)draw_countdown(next_u(st), K.f_lnq[s]) << 16);
-}
-
-// max |vx| of the first n particles of species s in cells per step, as the bits of a float
-// (non-negative floats order like their bit patterns; a non-finite value wins)
-__global__ void k_max_abs_vx32(DevCtx K, int s, long long n, unsigned long long* out) {
-  unsigned m = 0u;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x)
-    m = max(m, __float_as_uint(fabsf(K.ov[s][q].y)));
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, (unsigned long long)m);
+       q += (long long)gridDim.x * blockDim.x) {
+    const double xn = x[q] * K.inv_dx;
+    long long j = __double2ll_rd(xn);
+    if (j > K.nc - 1) j = K.nc - 1;
+    if (j < 0) j = 0;
+    const float off = (float)(xn - (double)j);
+    K.ov[s][q] = make_float2(off, (float)(vx[q] * sc));
+    K.fvy[s][q] = (float)(vy[q] * sc);
+    K.fvz[s][q] = (float)(vz[q] * sc);
+    const unsigned pid = id[q];
+    if (id != K.id[s]) K.id[s][q] = pid;
+    Stream st(K, s, kPurCount, pid, step);
+    K.ccd[s][q] = (unsigned)j | ((unsigned)draw_countdown(next_u(st), K.f_lnq[s]) << 16);
+    const int wr = __float2int_rn(off * 65536.0f);
+    atomicAdd(&csm[j], (unsigned long long)(65536 - wr) << 16);
+    atomicAdd(&csm[j + 1], (unsigned long long)wr << 16);
+  }
+  __syncthreads();
+  unsigned long long* C = K.C + (size_t)((step & 1u) * 2 + s) * nx;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x)
+    if (csm[j]) atomicAdd(&C[j], csm[j]);
 }
 
-// Sum of vx^2 + vy^2 + vz^2 over the first n particles of species s, in (cells per step)^2,
-// accumulated in double: one double atomic per block (a diagnostic only).
-__global__ void k_sum_v2_32(DevCtx K, int s, long long n, double* out) {
-  __shared__ double ws[kWarps32];
+// pic_diag in one launch.  Every block reduces the electrons' max |vx| (as the bits of a
+// non-negative float or double, which order like the values; a non-finite value wins) and
+// sum of |v|^2 over the live count into the state's reduction words; the last block to finish
+// (by a ticket) then writes the state, the event counters, the averages and the
+// distributions into `out` (the handle's pinned host buffer, device-mapped) at the byte
+// offsets off[0..4], and clears the reduction words and the ticket for the next call.
+template <bool F32>
+__global__ void __launch_bounds__(256) k_diag(DevCtx K, char* __restrict__ out, DiagOffsets off) {
+  __shared__ unsigned long long wm[8];
+  __shared__ double wsum[8];
+  __shared__ int last;
+  const long long n = K.st->n[0];
+  unsigned long long m = 0ull;
   double acc = 0.0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
-    const double a = K.ov[s][q].y, b = K.fvy[s][q], c = K.fvz[s][q];
+    double a, b, c;
+    if (F32) {
+      const float ax = K.ov[0][q].y;
+      m = max(m, (unsigned long long)__float_as_uint(fabsf(ax)));
+      a = ax;
+      b = K.fvy[0][q];
+      c = K.fvz[0][q];
+    } else {
+      a = K.vx[0][q];
+      m = max(m, (unsigned long long)__double_as_longlong(fabs(a)));
+      b = K.vy[0][q];
+      c = K.vz[0][q];
+    }
     acc += (a * a + b * b) + c * c;
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  for (int o = 16; o > 0; o >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    wm[w] = m;
+    wsum[w] = acc;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kWarps32; ++w) t += ws[w];
-    if (t != 0.0) atomicAdd(out, t);
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      m = max(m, wm[i]);
+      acc += wsum[i];
+    }
+    if (m) atomicMax(&K.st->vmax_bits, m);
+    if (acc != 0.0) atomicAdd(&K.st->v2sum, acc);
+    __threadfence();
+    last = atomicAdd(&K.st->diag_ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // L2 reads (__ldcg): this block read the state's line at its start
+  auto put = [&](size_t at, const void* src, size_t bytes) {
+    const unsigned long long* s8 = static_cast<const unsigned long long*>(src);
+    unsigned long long* d8 = reinterpret_cast<unsigned long long*>(out + at);
+    for (size_t i = threadIdx.x; i < bytes / 8; i += blockDim.x) d8[i] = __ldcg(s8 + i);
+  };
+  put(off.state, K.st, sizeof(DevState) / 8 * 8);
+  put(off.counters, K.counters, sizeof(unsigned long long) * kNumCounters);
+  put(off.acc, K.acc, sizeof(double) * 2 * (size_t)K.nx);
+  put(off.eepf, K.eepf, sizeof(unsigned long long) * (size_t)K.eepf_bins);
+  put(off.fedf, K.fedf, sizeof(unsigned long long) * 2 * (size_t)K.fedf_bins);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    K.st->vmax_bits = 0ull;
+    K.st->v2sum = 0.0;
+    K.st->diag_ticket = 0u;
   }
 }
 
-// FP32 cell units -> FP64 SI state, for pic_get_particles and the diagnostics.
 __global__ void k_to_fp64(DevCtx K, int s, long long n) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
@@ -973,24 +1037,6 @@ __global__ void k_to_fp64(DevCtx K, int s, long long n) {
 }
 
 // Deposit of the FP32 state with the FP32 rule (16-bit weights), after a load or a set.
-__global__ void k_deposit32(DevCtx K, int s, int buf, long long n) {
-  // block-private counts over a grid-stride loop, then one global atomic per touched node
-  extern __shared__ unsigned long long dsm32[];
-  const int nx = K.nx;
-  for (int j = threadIdx.x; j < nx; j += blockDim.x) dsm32[j] = 0ull;
-  __syncthreads();
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(K.ccd[s][q] & 0xFFFFu);
-    const int wr = __float2int_rn(K.ov[s][q].x * 65536.0f);
-    atomicAdd(&dsm32[j], (unsigned long long)(65536 - wr) << 16);
-    atomicAdd(&dsm32[j + 1], (unsigned long long)wr << 16);
-  }
-  __syncthreads();
-  unsigned long long* C = K.C + (size_t)(buf * 2 + s) * nx;
-  for (int j = threadIdx.x; j < nx; j += blockDim.x)
-    if (dsm32[j]) atomicAdd(&C[j], dsm32[j]);
-}
 
 // ------------------------------------------------------------ ensemble (one launch a step)
 // All blocks of the ensemble launch are resident together (cooperative launch), so they can
@@ -1331,33 +1377,30 @@ cudaError_t launch_convert(const DevCtx& K, int species, long long n, bool to_fp
   if (n <= 0) return cudaSuccess;
   const unsigned g = (unsigned)((n + 255) / 256);
   if (to_fp32)
-    k_to_fp32<<<g, 256, 0, s>>>(K, species, n);
+    return launch_convert_from(K, species, n, K.x[species], K.vx[species], K.vy[species],
+                               K.vz[species], K.id[species], s);
+  k_to_fp64<<<g, 256, 0, s>>>(K, species, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_from(const DevCtx& K, int species, long long n, const double* x,
+                                const double* vx, const double* vy, const double* vz,
+                                const unsigned* id, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + 255) / 256, 2 * kDepositBlocks);
+  k_to_fp32<<<(unsigned)blocks, 256, sizeof(unsigned long long) * K.nx, s>>>(K, species, n, x,
+                                                                            vx, vy, vz, id);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const DevCtx& K, bool fp32, char* out_dev, const DiagOffsets& off,
+                        cudaStream_t s) {
+  const long long want = (K.cap + 255) / 256;
+  const unsigned grid = (unsigned)(want < 1024 ? (want > 0 ? want : 1) : 1024);
+  if (fp32)
+    k_diag<true><<<grid, 256, 0, s>>>(K, out_dev, off);
   else
-    k_to_fp64<<<g, 256, 0, s>>>(K, species, n);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_max_abs_vx32(const DevCtx& K, int species, long long n,
-                                unsigned long long* out, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const long long want = (n + 255) / 256;
-  k_max_abs_vx32<<<(unsigned)(want < 1024 ? want : 1024), 256, 0, s>>>(K, species, n, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sum_v2_32(const DevCtx& K, int species, long long n, double* out,
-                             cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const long long want = (n + kBlock - 1) / kBlock;
-  k_sum_v2_32<<<(unsigned)(want < 1024 ? want : 1024), kBlock, 0, s>>>(K, species, n, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_deposit32(const DevCtx& K, int species, int buf, long long n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const long long blocks = std::min<long long>((n + 255) / 256, kDepositBlocks);
-  k_deposit32<<<(unsigned)blocks, 256, sizeof(unsigned long long) * K.nx, s>>>(K, species, buf,
-                                                                              n);
+    k_diag<false><<<grid, 256, 0, s>>>(K, out_dev, off);
   return cudaGetLastError();
 }
 

@@ -92,7 +92,9 @@ __global__ void k_init_load(DevCtx K, int s, long long n0) {
 
 __global__ void k_deposit(DevCtx K, int s, int buf, long long n) {
   // block-private counts over a grid-stride loop, then one global atomic per touched node
-  // (integer sums, so the order of the additions does not matter)
+  // (integer sums, so the order of the additions does not matter); buf < 0: the counts
+  // buffer of the current step
+  if (buf < 0) buf = (int)(K.st->step & 1u);
   extern __shared__ unsigned long long dsm[];
   const int nx = K.nx;
   for (int j = threadIdx.x; j < nx; j += blockDim.x) dsm[j] = 0ull;
@@ -104,6 +106,19 @@ __global__ void k_deposit(DevCtx K, int s, int buf, long long n) {
   unsigned long long* C = K.C + (size_t)(buf * 2 + s) * nx;
   for (int j = threadIdx.x; j < nx; j += blockDim.x)
     if (dsm[j]) atomicAdd(&C[j], dsm[j]);
+}
+
+// A species' population replaced (pic_set_particles): its count, the count the next particle
+// pass starts from, its next id, and its counts in the current step's buffer cleared for the
+// deposit that follows.
+__global__ void k_set_counts(DevCtx K, int s, long long n, unsigned next_id) {
+  if (threadIdx.x == 0) {
+    K.st->n[s] = n;
+    K.st->n_snap[s] = n;
+    K.st->next_id[s] = next_id;
+  }
+  unsigned long long* C = K.C + (size_t)((K.st->step & 1u) * 2 + s) * K.nx;
+  for (int j = threadIdx.x; j < K.nx; j += blockDim.x) C[j] = 0ull;
 }
 
 // Counts live in buffer (step & 1) and the other buffer must be zero (it receives the next
@@ -120,40 +135,6 @@ __global__ void k_set_step(DevCtx K, unsigned step) {
   }
   __syncthreads();
   if (threadIdx.x == 0) K.st->step = step;
-}
-
-// max |v| over n values: non-negative doubles order like their bit patterns
-__global__ void k_max_abs(const double* __restrict__ v, long long n, unsigned long long* out) {
-  unsigned long long m = 0ull;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x)
-    m = max(m, (unsigned long long)__double_as_longlong(fabs(v[q])));
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
-}
-
-// Sum of vx^2 + vy^2 + vz^2 over the first n particles of species s (FP64 SI state): one
-// double atomic per block, so the last bits depend on the block order (a diagnostic only).
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double ws[32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-  return t;  // valid in thread 0
-}
-
-__global__ void k_sum_v2(DevCtx K, int s, long long n, double* out) {
-  double acc = 0.0;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    const double a = K.vx[s][q], b = K.vy[s][q], c = K.vz[s][q];
-    acc += (a * a + b * b) + c * c;
-  }
-  const double t = block_sum(acc);
-  if (threadIdx.x == 0 && t != 0.0) atomicAdd(out, t);
 }
 
 // Stand-alone field solve for the current step (after init, set_particles, set_step, or on
@@ -549,20 +530,9 @@ cudaError_t launch_set_step(const DevCtx& K, unsigned step, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_max_abs(const double* v, long long n, unsigned long long* out,
-                           cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const long long want = (n + 255) / 256;
-  const unsigned grid = (unsigned)(want < 1024 ? want : 1024);
-  k_max_abs<<<grid, 256, 0, s>>>(v, n, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sum_v2(const DevCtx& K, int species, long long n, double* out,
-                          cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const long long want = (n + 255) / 256;
-  k_sum_v2<<<(unsigned)(want < 1024 ? want : 1024), 256, 0, s>>>(K, species, n, out);
+cudaError_t launch_set_counts(const DevCtx& K, int species, long long n, unsigned next_id,
+                              cudaStream_t s) {
+  k_set_counts<<<1, 256, 0, s>>>(K, species, n, next_id);
   return cudaGetLastError();
 }
 

@@ -62,6 +62,13 @@ class PicDiagOut(C.Structure):
     ]
 
 
+# pic_diag_out's scalar fields (everything but the array pointers, their lengths and the
+# counters)
+_DIAG_SCALARS = tuple(n for n, _ in PicDiagOut._fields_
+                      if n not in ("n_e", "n_i", "eepf_energy", "eepf", "fedf_energy", "fedf_e",
+                                   "fedf_i", "n_x", "eepf_bins", "fedf_bins", "counters"))
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -313,23 +320,24 @@ class Simulation:
         return dict(zip(("dt", "dx", "ng", "numax_e", "numax_i", "pmax_e", "pmax_i"),
                         out.tolist()))
 
+    _DIAG_ARRAYS = ("n_e", "n_i", "eepf_energy", "eepf", "fedf_energy", "fedf_e", "fedf_i")
+
     def diag(self) -> dict:
         c = self.cfg
-        arrs = dict(n_e=np.zeros(self.nx), n_i=np.zeros(self.nx),
-                    eepf_energy=np.zeros(c["eepf_bins"]), eepf=np.zeros(c["eepf_bins"]),
-                    fedf_energy=np.zeros(c["fedf_bins"]), fedf_e=np.zeros(c["fedf_bins"]),
-                    fedf_i=np.zeros(c["fedf_bins"]))
+        nx, ne, nf = self.nx, c["eepf_bins"], c["fedf_bins"]
+        # one buffer for the seven arrays pic_diag fills completely
+        buf = np.empty(2 * nx + 2 * ne + 3 * nf)
+        cuts = np.cumsum([0, nx, nx, ne, ne, nf, nf, nf])
+        arrs = {k: buf[cuts[i]:cuts[i + 1]] for i, k in enumerate(self._DIAG_ARRAYS)}
         d = PicDiagOut()
-        d.n_x, d.eepf_bins, d.fedf_bins = self.nx, c["eepf_bins"], c["fedf_bins"]
+        d.n_x, d.eepf_bins, d.fedf_bins = nx, ne, nf
         for k, a in arrs.items():
             setattr(d, k, a.ctypes.data_as(_DP))
         rc = _check(lib().pic_diag(self._h, C.byref(d)), "pic_diag")
         out = dict(arrs)
-        for name, _ in PicDiagOut._fields_:
-            if name in arrs or name in ("n_x", "eepf_bins", "fedf_bins"):
-                continue
-            v = getattr(d, name)
-            out[name] = np.array(v[:], dtype=np.uint64) if name == "counters" else v
+        for name in _DIAG_SCALARS:
+            out[name] = getattr(d, name)
+        out["counters"] = np.ctypeslib.as_array(d.counters).astype(np.uint64)
         out["return_code"] = rc
         return out
 
