@@ -729,6 +729,9 @@ def main():
         dist.destroy_process_group()
 
 
+E2E_WARMUP = 3  # untimed end-to-end iterations before the timed ones
+
+
 def run_e2e(sim, args, torch):
     """End to end through the C-ABI with host buffers: each step uploads the particle state
     from pinned host memory (pic_set_particles), advances one step (pic_step) and reads the
@@ -749,22 +752,27 @@ def run_e2e(sim, args, torch):
     nx = sim.nx
     c = sim.cfg
     d2h = 8 * (2 * nx + c["eepf_bins"] + 2 * c["fedf_bins"] + 16) + 72
-    parts = 0
-    times = []
-    for _ in range(args.e2e_steps):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
+    def e2e_step():
         for s in (0, 1):
             a = host[s]
             n = len(a["x"][1])
             sim.set_particles(s, a["x"][1], a["vx"][1], a["vy"][1], a["vz"][1], a["id"][1], n)
         sim.step(1)
         sim.diag()
+
+    for _ in range(E2E_WARMUP):  # untimed, like every other measurement's warm-up
+        e2e_step()
+    parts = 0
+    times = []
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        e2e_step()
         times.append(time.perf_counter() - t)
         parts += len(host[0]["x"][1]) + len(host[1]["x"][1])
     total = sum(times)
     return {"value": parts / total, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+            "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "warmup": E2E_WARMUP,
             "note": "wall clock per step: H2D of the full particle state from pinned memory, "
                     "one step, pic_diag read-back"}
 
