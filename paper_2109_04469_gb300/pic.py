@@ -323,21 +323,27 @@ class Simulation:
     _DIAG_ARRAYS = ("n_e", "n_i", "eepf_energy", "eepf", "fedf_energy", "fedf_e", "fedf_i")
 
     def diag(self) -> dict:
-        c = self.cfg
-        nx, ne, nf = self.nx, c["eepf_bins"], c["fedf_bins"]
-        # one buffer for the seven arrays pic_diag fills completely
-        buf = np.empty(2 * nx + 2 * ne + 3 * nf)
-        cuts = np.cumsum([0, nx, nx, ne, ne, nf, nf, nf])
-        arrs = {k: buf[cuts[i]:cuts[i + 1]] for i, k in enumerate(self._DIAG_ARRAYS)}
-        d = PicDiagOut()
-        d.n_x, d.eepf_bins, d.fedf_bins = nx, ne, nf
-        for k, a in arrs.items():
-            setattr(d, k, a.ctypes.data_as(_DP))
+        d = getattr(self, "_diag_out", None)
+        if d is None:  # one output struct per simulation, its array lengths set once
+            c = self.cfg
+            d = self._diag_out = PicDiagOut()
+            d.n_x, d.eepf_bins, d.fedf_bins = self.nx, c["eepf_bins"], c["fedf_bins"]
+            n = (self.nx, self.nx, c["eepf_bins"], c["eepf_bins"], c["fedf_bins"],
+                 c["fedf_bins"], c["fedf_bins"])
+            self._diag_cuts = [int(v) for v in np.cumsum((0,) + n)]
+        cuts = self._diag_cuts
+        # fresh arrays every call (the caller may keep them), all seven in one buffer that
+        # pic_diag fills completely
+        buf = np.empty(cuts[-1])
+        base = buf.ctypes.data
+        out = {}
+        for i, k in enumerate(self._DIAG_ARRAYS):
+            out[k] = buf[cuts[i]:cuts[i + 1]]
+            setattr(d, k, C.cast(base + 8 * cuts[i], _DP))
         rc = _check(lib().pic_diag(self._h, C.byref(d)), "pic_diag")
-        out = dict(arrs)
         for name in _DIAG_SCALARS:
             out[name] = getattr(d, name)
-        out["counters"] = np.ctypeslib.as_array(d.counters).astype(np.uint64)
+        out["counters"] = np.array(d.counters, dtype=np.uint64)
         out["return_code"] = rc
         return out
 
