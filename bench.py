@@ -169,6 +169,19 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+BAD_CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clocks_rejected(c: dict) -> bool:
+    """A timed region whose clock samples show a hardware or thermal slowdown, or an SM clock
+    well below its maximum with no reason given (a leftover clock lock), is not kept
+    (sw_power_cap is kept and noted)."""
+    if any(r in c.get("reasons", []) for r in BAD_CLOCK_REASONS):
+        return True
+    sm, smax = c.get("sm_mhz"), c.get("sm_max_mhz")
+    return bool(sm and smax and sm < 0.9 * smax and not c.get("reasons"))
+
+
 def cpu_baseline(cfg: dict, steps: int, warmup: int = 2) -> dict:
     """The FP64 oracle as it stands, one thread, on the full workload for a bounded window."""
     from oracle import oracle as O
@@ -633,8 +646,18 @@ def main():
     pcfg = {k: v for k, v in cfg.items() if k != "name"}
     runs = {}
     for prec in args.precisions.split(","):
-        runs[prec] = measure(pcfg, prec, args, torch, dist, local_rank,
-                             with_e2e=(prec == args.precisions.split(",")[0] and not args.no_e2e))
+        e2e = prec == args.precisions.split(",")[0] and not args.no_e2e
+        r = measure(pcfg, prec, args, torch, dist, local_rank, with_e2e=e2e)
+        bad = clocks_rejected(r["clocks"])
+        if dist:  # every rank measures again if any rank's clocks were off
+            flag = torch.tensor([int(bad)], device="cuda")
+            dist.all_reduce(flag, op=dist.ReduceOp.MAX)
+            bad = bool(flag.item())
+        if bad:  # measured again once; the line says so
+            r = measure(pcfg, prec, args, torch, dist, local_rank, with_e2e=e2e)
+            r["clocks"]["remeasured"] = True
+        r["clocks"]["rejected"] = clocks_rejected(r["clocks"])
+        runs[prec] = r
     head_prec = args.precisions.split(",")[0]
     head = runs[head_prec]
     total_ms, total_parts = reduce_ranks(torch, dist, head["step_ms"], head["parts"])

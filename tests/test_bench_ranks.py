@@ -73,3 +73,19 @@ def test_ensemble_cpu_baseline_uses_every_thread():
     r = bench.ensemble_cpu_baseline(4, budget_s=0.5)
     assert r["kind"] == "oracle" and r["unit"] == "particle-steps/s"
     assert 1 <= r["cores"] <= 4 and r["value"] > 0
+
+
+def test_clock_samples_that_reject_a_timed_region():
+    """A hardware or thermal slowdown, or an SM clock well below its maximum with no reason
+    given (a leftover lock), rejects the timed region (bench.py measures it once more); a
+    power cap is kept."""
+    import bench
+
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=1900.0, reasons=["sw_power_cap"]))
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1500.0))
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(ok, reasons=[r]))
+    assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None,
+                                      "reasons": ["nvidia-smi unavailable"]})
