@@ -1013,7 +1013,8 @@ __global__ void __launch_bounds__(256) k_diag(DevCtx K, char* __restrict__ out, 
     unsigned long long* d8 = reinterpret_cast<unsigned long long*>(out + at);
     for (size_t i = threadIdx.x; i < bytes / 8; i += blockDim.x) d8[i] = __ldcg(s8 + i);
   };
-  put(off.state, K.st, sizeof(DevState) / 8 * 8);
+  static_assert(sizeof(DevState) % 8 == 0, "the state is copied in 8-byte words");
+  put(off.state, K.st, sizeof(DevState));
   put(off.counters, K.counters, sizeof(unsigned long long) * kNumCounters);
   put(off.acc, K.acc, sizeof(double) * 2 * (size_t)K.nx);
   put(off.eepf, K.eepf, sizeof(unsigned long long) * (size_t)K.eepf_bins);
