@@ -466,6 +466,7 @@ int pic_init(const pic_params* p, void* workspace, size_t workspace_bytes, void*
   // hole / birth list owners: the particle blocks (the FP32 pass packs its warps' lists)
   K.nlist = h->push_grid;
   K.gw_div = make_divider((long long)h->push_grid * (kBlock / 32));
+  K.nl_div = make_divider(K.nlist);
   set_list_counts(K, K.nlist);
   h->K = K;
   if ((fp32 ? configure_place_fp32(nx, K.nlist) : configure_place_fp64(nx, K.nlist)) !=

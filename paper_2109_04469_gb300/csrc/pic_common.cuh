@@ -322,6 +322,17 @@ __host__ __device__ __forceinline__ size_t place_smem_bytes(int nx, int nlist) {
 // Row stride, in ints, of the five prefix arrays in shared memory (16-byte rows).
 __host__ __device__ __forceinline__ int prefix_stride(int G) { return (G + 3) & ~3; }
 
+// The single run's placement launch also keeps the list bases of its nlist owners in shared
+// memory, after the five prefix arrays: sb[s * prefix_stride(G + 1) + b] = list_base(N_s, b,
+// G) for b = 0..G, formed once per block (multiply-high by K.nl_div) instead of by 64-bit
+// divisions in every item.
+__host__ __device__ __forceinline__ size_t place_run_smem_bytes(int nx, int nlist) {
+  const size_t field = sizeof(__int128) * (size_t)nx;
+  const size_t lists = sizeof(int) * (5 * (size_t)prefix_stride(nlist) +
+                                      2 * (size_t)prefix_stride(nlist + 1));
+  return field > lists ? field : lists;
+}
+
 // Reading C-15, run by every placement block into its own shared memory: the exclusive
 // prefixes of the five per-owner count arrays of one simulation (sp[a * Gp + c], Gp =
 // prefix_stride(G): a = 0, 1 holes of electrons / ions; 2 electron births from electron
@@ -329,7 +340,7 @@ __host__ __device__ __forceinline__ int prefix_stride(int G) { return (G + 3) & 
 // births) and the totals of both species.  The count arrays lie at stride gstride from
 // hole_cnt[0] (gstride >= G + 4 or the block is padded); they are read once with 16-byte
 // loads; nothing waits on another block.
-template <int NT>
+template <int NT, bool kSB = false>
 __device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, CompactTot* sT) {
   constexpr int kA = 5, NW = NT / 32;
   __shared__ int wsum[NW][kA], wtot[kA];
@@ -381,6 +392,13 @@ __device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, Comp
       sp[a * Gp + c] = __ldcg(K.hole_cnt[0] + (size_t)a * gstride + c);
     }
   }
+  const int Gb = prefix_stride(G + 1);
+  int* sb = sp + kA * Gp;  // list bases (kSB), formed while the staging loads are in flight
+  if (kSB)
+    for (int i = threadIdx.x; i < 2 * (G + 1); i += NT) {
+      const int s = i > G ? 1 : 0, b = i - s * (G + 1);
+      sb[s * Gb + b] = (int)range_begin_d(N2[s], b, K.nl_div);
+    }
   if (threadIdx.x < 2) sq[threadIdx.x] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -460,9 +478,9 @@ __device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, Comp
     Nn2[s] = N2[s] - H2[s] + Beff2[s];
     owner[s] = -1;
     if (H2[s] > Beff2[s]) {
-      const int b = range_owner(N2[s], Nn2[s], G);
+      const int b = kSB ? upper_bound_i(sb + s * Gb, G, Nn2[s]) - 1 : range_owner(N2[s], Nn2[s], G);
       owner[s] = b;
-      const int* list = K.hole_idx[s] + list_base(N2[s], b, G);
+      const int* list = K.hole_idx[s] + (kSB ? (long long)sb[s * Gb + b] : list_base(N2[s], b, G));
       const int m = (b + 1 < G ? sp[s * Gp + b + 1] : H2[s]) - sp[s * Gp + b];
       unsigned below = 0;
       for (int r = threadIdx.x; r < m; r += NT) below += ((long long)list[r] < Nn2[s]) ? 1u : 0u;
@@ -489,10 +507,14 @@ __device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, Comp
 }
 
 // Index of the hole of rank r of species s (hp: that species' hole prefixes, G owners).
+// sbs: that species' list bases in shared memory (kSB), else null.
+template <bool kSB>
 __device__ __forceinline__ long long hole_of_rank(const DevCtx& K, int G, const int* hp, int s,
-                                                  long long r, const CompactTot& t) {
+                                                  long long r, const CompactTot& t,
+                                                  const int* sbs) {
   const int b = upper_bound_i(hp, G, r) - 1;
-  return K.hole_idx[s][list_base(t.N, b, G) + (r - hp[b])];
+  const long long base = kSB ? (long long)sbs[b] : list_base(t.N, b, G);
+  return K.hole_idx[s][base + (r - hp[b])];
 }
 
 // Births and tail survivors of one simulation to place: births into the holes by rank, then
@@ -516,13 +538,18 @@ __device__ __forceinline__ void publish_counts(const DevCtx& K, int s, const Com
 
 // Items u = first, first + step, ... below end of the placement of one simulation (items in
 // the order: electron births, electron tail moves, ion births, ion tail moves).  P supplies
-// the record moves of the particle representation: P::birth(K, s, list, slot, d, id) and
-// P::move(K, s, t, d).
-template <class P>
+// the records of the particle representation: P::Rec, P::load_birth(K, list, slot) (a birth
+// record), P::load(K, s, t) (the particle at slot t) and P::store(K, s, d, rec, id).  An
+// item's record is loaded before the hole searches that give its destination, so that its
+// loads are in flight during theirs (a tail position's record is loaded even when that
+// position turns out to be a hole, and then dropped).
+template <class P, bool kSB = false>
 __device__ __forceinline__ void place_items(const DevCtx& K, int G, const int* sp,
                                             const CompactTot* sT, long long first,
                                             long long end, long long step) {
   const int Gp = prefix_stride(G);
+  const int* sb = sp + 5 * Gp;  // list bases of both species (kSB)
+  const int Gb = prefix_stride(G + 1);
   const CompactTot &te = sT[0], &ti = sT[1];  // shared: no per-thread copies
   const long long tle = te.H > te.Beff ? te.N - te.Nn : 0;
   for (long long u = first; u < end; u += step) {
@@ -541,6 +568,7 @@ __device__ __forceinline__ void place_items(const DevCtx& K, int G, const int* s
     }
     const CompactTot& t = sT[s];
     const int* hp = sp + s * Gp;
+    const int* sbs = sb + s * Gb;
     if (birth) {
       const long long r = v;
       int list, b;
@@ -550,29 +578,32 @@ __device__ __forceinline__ void place_items(const DevCtx& K, int G, const int* s
       if (s == 0 && r < t.B0) {
         list = 0;
         b = upper_bound_i(sp + 2 * Gp, G, r) - 1;
-        slot = list_base(te.N, b, G) + (r - sp[2 * Gp + b]);
+        slot = (kSB ? (long long)sb[b] : list_base(te.N, b, G)) + (r - sp[2 * Gp + b]);
       } else if (s == 0) {
         list = 1;
         b = upper_bound_i(sp + 3 * Gp, G, r) - 1;
-        slot = list_base(ti.N, b, G) + (r - sp[3 * Gp + b]);
+        slot = (kSB ? (long long)sb[Gb + b] : list_base(ti.N, b, G)) + (r - sp[3 * Gp + b]);
       } else {
         list = 2;
         b = upper_bound_i(sp + 4 * Gp, G, r) - 1;
-        slot = list_base(te.N, b, G) + (r - sp[4 * Gp + b]);
+        slot = (kSB ? (long long)sb[b] : list_base(te.N, b, G)) + (r - sp[4 * Gp + b]);
       }
-      const long long d = (r < t.H) ? hole_of_rank(K, G, hp, s, r, t) : t.N + r - t.H;
-      P::birth(K, s, list, slot, d, t.nid + (unsigned)r);
+      const typename P::Rec rec = P::load_birth(K, list, slot);
+      const long long d =
+          (r < t.H) ? hole_of_rank<kSB>(K, G, hp, s, r, t, sbs) : t.N + r - t.H;
+      P::store(K, s, d, rec, t.nid + (unsigned)r);
     } else {
       const long long idx = t.Nn + v;  // a tail position
-      const int b = range_owner(t.N, idx, G);
-      const int* list = K.hole_idx[s] + list_base(t.N, b, G);
+      const typename P::Rec rec = P::load(K, s, idx);
+      const int b = kSB ? upper_bound_i(sbs, G, idx) - 1 : range_owner(t.N, idx, G);
+      const int* list = K.hole_idx[s] + (kSB ? (long long)sbs[b] : list_base(t.N, b, G));
       const int m = (b + 1 < G ? hp[b + 1] : (int)t.H) - hp[b];
       bool is_hole;
       const int lb = find_sorted(list, m, idx, is_hole);
       if (is_hole) continue;  // the tail position is itself a hole
       const long long before = (long long)hp[b] + lb;  // holes below idx
       const long long j = (idx - t.Nn) - (before - t.q);  // rank among survivors
-      P::move(K, s, idx, hole_of_rank(K, G, hp, s, t.Beff + j, t));
+      P::store(K, s, hole_of_rank<kSB>(K, G, hp, s, t.Beff + j, t, sbs), rec, rec.id);
     }
   }
 }
@@ -592,10 +623,10 @@ __global__ void __launch_bounds__(256) k_place_field(DevCtx K) {
   }
   __shared__ CompactTot sT[2];
   int* sp = reinterpret_cast<int*>(place_smem);
-  list_prefixes<256>(K, K.nlist, K.nlist, sp, sT);
+  list_prefixes<256, true>(K, K.nlist, K.nlist, sp, sT);
   const int b = blockIdx.x - F;
   if (b == 0 && threadIdx.x < 2) publish_counts(K, threadIdx.x, sT[threadIdx.x]);
-  place_items<P>(K, K.nlist, sp, sT, (long long)b * blockDim.x + threadIdx.x, place_count(sT),
+  place_items<P, true>(K, K.nlist, sp, sT, (long long)b * blockDim.x + threadIdx.x, place_count(sT),
                  (long long)(gridDim.x - F) * blockDim.x);
 }
 

@@ -166,6 +166,7 @@ struct DevCtx {
   // owner ([nlist] entries); the placement launch forms their prefixes in shared memory.
   int nlist;            // list owners of the particle pass
   Divider gw_div;       // divider of the FP32 particle grid's warp count
+  Divider nl_div;       // divider of nlist
   int nfield;           // field blocks of the placement launch
   int *hole_idx[2];     // [cap]: hole indices
   int *hole_cnt[2];

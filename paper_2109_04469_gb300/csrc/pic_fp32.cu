@@ -887,28 +887,29 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
 // Record moves of the FP32 representation for the placement launch.
 struct Fp32Moves {
   static constexpr bool kFieldMul = true;  // FP32 kicks: the field solve multiplies
-  // every field is loaded before the first store, so the loads are in flight together
-  static __device__ __forceinline__ void birth(const DevCtx& K, int s, int list, long long slot,
-                                               long long d, unsigned id) {
+  struct Rec {
+    unsigned ccd, id;
+    float2 ov;
+    float vy, vz;
+  };
+  // every field is loaded before the first use, so the loads are in flight together
+  static __device__ __forceinline__ Rec load_birth(const DevCtx& K, int list, long long slot) {
     const float* rec = list == 0 ? K.feb[0] : (list == 1 ? K.feb[1] : K.fib);
     const size_t cap = (size_t)K.nchunk_max * kChunk;
     const float c = rec[slot], o = rec[slot + cap], vx = rec[slot + 2 * cap],
                 vy = rec[slot + 3 * cap], vz = rec[slot + 4 * cap], cd = rec[slot + 5 * cap];
-    K.ccd[s][d] = (unsigned)__float_as_int(c) | ((unsigned)__float_as_int(cd) << 16);
-    K.ov[s][d] = make_float2(o, vx);
-    K.fvy[s][d] = vy;
-    K.fvz[s][d] = vz;
-    K.id[s][d] = id;
+    return Rec{(unsigned)__float_as_int(c) | ((unsigned)__float_as_int(cd) << 16), 0u,
+               make_float2(o, vx), vy, vz};
   }
-  static __device__ __forceinline__ void move(const DevCtx& K, int s, long long t, long long d) {
-    const unsigned ccd = K.ccd[s][t];
-    const float2 ov = K.ov[s][t];
-    const float vy = K.fvy[s][t], vz = K.fvz[s][t];
-    const unsigned id = K.id[s][t];
-    K.ccd[s][d] = ccd;
-    K.ov[s][d] = ov;
-    K.fvy[s][d] = vy;
-    K.fvz[s][d] = vz;
+  static __device__ __forceinline__ Rec load(const DevCtx& K, int s, long long t) {
+    return Rec{K.ccd[s][t], K.id[s][t], K.ov[s][t], K.fvy[s][t], K.fvz[s][t]};
+  }
+  static __device__ __forceinline__ void store(const DevCtx& K, int s, long long d,
+                                               const Rec& r, unsigned id) {
+    K.ccd[s][d] = r.ccd;
+    K.ov[s][d] = r.ov;
+    K.fvy[s][d] = r.vy;
+    K.fvz[s][d] = r.vz;
     K.id[s][d] = id;
   }
 };
@@ -1336,7 +1337,7 @@ cudaError_t launch_push_fp32(const DevCtx& K, int grid, cudaStream_t s) {
 
 cudaError_t launch_place_fp32(const DevCtx& K, int grid, cudaStream_t s) {
   return launch_chained(k_place_field<Fp32Moves>, (unsigned)grid, 256u,
-                        place_smem_bytes(K.nx, K.nlist), s, K);
+                        place_run_smem_bytes(K.nx, K.nlist), s, K);
 }
 
 size_t ensemble_pipes_offset(int nx_max) { return pipes_offset(nx_max); }
@@ -1411,7 +1412,7 @@ cudaError_t configure_kernels32(int nx) {
 }
 
 cudaError_t configure_place_fp32(int nx, int nlist) {
-  return raise_smem_limit(k_place_field<Fp32Moves>, (int)place_smem_bytes(nx, nlist));
+  return raise_smem_limit(k_place_field<Fp32Moves>, (int)place_run_smem_bytes(nx, nlist));
 }
 
 int push_fp32_blocks_per_sm(int nx) {

@@ -466,26 +466,25 @@ __global__ void __launch_bounds__(kBlock, 2) k_push_fp64(DevCtx K) {
 // Record moves of the FP64 representation for the placement launch.
 struct Fp64Moves {
   static constexpr bool kFieldMul = false;  // bit-exact with the oracle: the field solve divides
-  // every field is loaded before the first store, so the loads are in flight together
-  static __device__ __forceinline__ void birth(const DevCtx& K, int s, int list, long long slot,
-                                               long long d, unsigned id) {
+  struct Rec {
+    double x, vx, vy, vz;
+    unsigned id;
+  };
+  // every field is loaded before the first use, so the loads are in flight together
+  static __device__ __forceinline__ Rec load_birth(const DevCtx& K, int list, long long slot) {
     const double* rec = list == 0 ? K.eb[0] : (list == 1 ? K.eb[1] : K.ib);
     const size_t cap = (size_t)K.nchunk_max * kChunk;
-    const double x = rec[slot], vx = rec[slot + cap], vy = rec[slot + 2 * cap],
-                 vz = rec[slot + 3 * cap];
-    K.x[s][d] = x;
-    K.vx[s][d] = vx;
-    K.vy[s][d] = vy;
-    K.vz[s][d] = vz;
-    K.id[s][d] = id;
+    return Rec{rec[slot], rec[slot + cap], rec[slot + 2 * cap], rec[slot + 3 * cap], 0u};
   }
-  static __device__ __forceinline__ void move(const DevCtx& K, int s, long long t, long long d) {
-    const double x = K.x[s][t], vx = K.vx[s][t], vy = K.vy[s][t], vz = K.vz[s][t];
-    const unsigned id = K.id[s][t];
-    K.x[s][d] = x;
-    K.vx[s][d] = vx;
-    K.vy[s][d] = vy;
-    K.vz[s][d] = vz;
+  static __device__ __forceinline__ Rec load(const DevCtx& K, int s, long long t) {
+    return Rec{K.x[s][t], K.vx[s][t], K.vy[s][t], K.vz[s][t], K.id[s][t]};
+  }
+  static __device__ __forceinline__ void store(const DevCtx& K, int s, long long d,
+                                               const Rec& r, unsigned id) {
+    K.x[s][d] = r.x;
+    K.vx[s][d] = r.vx;
+    K.vy[s][d] = r.vy;
+    K.vz[s][d] = r.vz;
     K.id[s][d] = id;
   }
 };
@@ -522,7 +521,7 @@ cudaError_t launch_push_fp64(const DevCtx& K, int grid, cudaStream_t s) {
 
 cudaError_t launch_place_fp64(const DevCtx& K, int grid, cudaStream_t s) {
   return launch_chained(k_place_field<Fp64Moves>, (unsigned)grid, 256u,
-                        place_smem_bytes(K.nx, K.nlist), s, K);
+                        place_run_smem_bytes(K.nx, K.nlist), s, K);
 }
 
 cudaError_t launch_set_step(const DevCtx& K, unsigned step, cudaStream_t s) {
@@ -592,7 +591,7 @@ cudaError_t configure_kernels(int nx) {
 }
 
 cudaError_t configure_place_fp64(int nx, int nlist) {
-  return raise_smem_limit(k_place_field<Fp64Moves>, (int)place_smem_bytes(nx, nlist));
+  return raise_smem_limit(k_place_field<Fp64Moves>, (int)place_run_smem_bytes(nx, nlist));
 }
 
 int push_fp64_blocks_per_sm(int nx) {
