@@ -298,7 +298,7 @@ int pic_ensemble_workspace_bytes(int n, size_t* bytes);
  * Records the step launch as a CUDA graph (falls back to direct launches if recording
  * fails).  Synchronises the stream.  PIC_ERR_PARAM for a member that is not PIC_FP32, on
  * another stream, repeated, or too large for the launch's shared memory (more than about
- * 4000 x 3800 / 2 superparticles of capacity per species); PIC_ERR_WORKSPACE for a missing
+ * 7900 x 3800 superparticles of capacity per species); PIC_ERR_WORKSPACE for a missing
  * or small workspace. */
 int pic_ensemble_create(pic_handle* const* sims, int n, const int64_t* target_steps,
                         void* workspace, size_t workspace_bytes, pic_ensemble** out);
@@ -311,12 +311,12 @@ int pic_ensemble_step(pic_ensemble* e, int64_t n_steps);
  * else the first non-OK member status. */
 int pic_ensemble_sync(pic_ensemble* e);
 
-/* Schedule: particles per list owner (256..4000), blocks per SM (1 or 2, as resources allow)
+/* Schedule: particles per list owner (256..16000), blocks per SM (1 or 2, as resources allow)
  * and whether to replay a CUDA graph.  Synchronises.  Results do not depend on it. */
 int pic_ensemble_configure(pic_ensemble* e, int32_t unit, int32_t blocks_per_sm,
                            int32_t use_graph);
 
-/* Time each schedule of the tuning space (unit 1024 / 2048 / 4000 x 1..2 blocks per SM)
+/* Time each schedule of the tuning space (unit 4000 / 8000 / 16000 x 1..2 blocks per SM)
  * over trial_steps real steps of the ensemble (the members advance by those steps) and keep
  * the fastest; chosen[0] = unit, chosen[1] = blocks per SM (chosen may be NULL). */
 int pic_ensemble_autotune(pic_ensemble* e, int32_t trial_steps, int32_t* chosen);

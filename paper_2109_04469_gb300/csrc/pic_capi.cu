@@ -1156,7 +1156,7 @@ int pic_ensemble_create(pic_handle* const* sims, int n, const int64_t* target_st
     h->gcap[i] = (int)std::min<long long>(nl - 4, gcap_lim);
     h->gstride[i] = (int)nl;
     // with at most gcap owners, an owner must still fit the shared counters' bound
-    if ((2 * sims[i]->p.capacity_per_species + h->gcap[i] - 1) / h->gcap[i] + 64 > kMaxEnsUnit)
+    if ((sims[i]->p.capacity_per_species + h->gcap[i] - 1) / h->gcap[i] + 64 > kEnsSpeciesRound)
       return fail(PIC_ERR_PARAM);
   }
   // phase-1 order: members whose electrons are collision candidates most often (the costly
@@ -1211,7 +1211,7 @@ int pic_ensemble_sync(pic_ensemble* e) {
 
 int pic_ensemble_autotune(pic_ensemble* e, int32_t trial_steps, int32_t* chosen) {
   if (!e || trial_steps < 1) return PIC_ERR_PARAM;
-  const int32_t units[3] = {1024, 2048, 4000};
+  const int32_t units[3] = {4000, 8000, 16000};
   float best = 0.0f;
   int32_t bu = e->unit, bb = e->bps;
   cudaEvent_t a = nullptr, b = nullptr;

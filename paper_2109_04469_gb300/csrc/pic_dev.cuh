@@ -114,7 +114,11 @@ struct DevState {
 // paper's parameter scans, §3): the simulations' own contexts and states, and the few words
 // the launch shares between its blocks.
 constexpr int kMaxEnsemble = 128;
-constexpr int kMaxEnsUnit = 4000;  // particles per list owner: keeps the 32-bit counters safe
+constexpr int kMaxEnsUnit = 16000;  // most particles (both species) per list owner
+// Particles of one species a warp of the ensemble handles between flushes of its block's
+// 32-bit counts: 8 warps x 8000 particles x 2^16 (a particle adds at most 2^16 to one count)
+// stays below 2^32.
+constexpr int kEnsSpeciesRound = 8000;
 struct DevCtx;
 struct EnsDev {
   unsigned estep;      // launches so far (parity selects the totals buffer)

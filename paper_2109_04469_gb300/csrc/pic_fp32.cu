@@ -1180,18 +1180,23 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
     const unsigned step = st->step;
     const long long ne = st->n[0], ni = st->n[1];
     const bool active = (long long)step < E->target[s];
+    // owners of about E->unit particles, and enough of them that no owner holds more than
+    // kEnsSpeciesRound - 64 particles of one species before the 32-particle rounding
+    const long long nmax = ne > ni ? ne : ni;
     long long g = (ne + ni + E->unit - 1) / E->unit;
+    g = max(g, (nmax + kEnsSpeciesRound - 65) / (kEnsSpeciesRound - 64));
     g = g < 1 ? 1 : (g > E->gcap[s] ? E->gcap[s] : g);
     sNe[s] = ne;
     sNi[s] = ni;
     sStep[s] = step;
     sG[s] = active ? (int)g : 0;
     sGd[s] = make_divider(g);
-    // owners per warp between counter flushes: every owner holds at most
-    // ceil(N / G) + 64 particles (32-particle rounding per species); keep the warp's sum
-    // within kMaxEnsUnit so the 32-bit shared counters stay in range
-    const long long per = (ne + ni + g - 1) / g + 64;
-    sUpw[s] = (int)max(1ll, (long long)kMaxEnsUnit / per);
+    // owners per warp between counter flushes: an owner's range of species s holds fewer
+    // than ceil(n_s / G) + 64 particles (32-particle rounding); keep the warp's sum within
+    // kEnsSpeciesRound so the 32-bit shared counters stay in range (per <= kEnsSpeciesRound
+    // by the owner count above, and the capacity check at creation)
+    const long long per = (nmax + g - 1) / g + 64;
+    sUpw[s] = (int)max(1ll, (long long)kEnsSpeciesRound / per);
     if (active && blockIdx.x == 0) snapshot_pass(*E->sims[s], step, ne, ni);
   }
   if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
