@@ -116,8 +116,8 @@ struct DevState {
 constexpr int kMaxEnsemble = 128;
 constexpr int kMaxEnsUnit = 16000;  // most particles (both species) per list owner
 // Particles of one species a warp of the ensemble handles between flushes of its block's
-// 32-bit counts: 8 warps x 8000 particles x 2^16 (a particle adds at most 2^16 to one count)
-// stays below 2^32.
+// 32-bit counts: 8 warps x 8000 particles x 2^16 stays below 2^32 (a particle adds at most
+// 2^16 to one count of its own species; births add theirs straight to the 64-bit counts).
 constexpr int kEnsSpeciesRound = 8000;
 struct DevCtx;
 struct EnsDev {

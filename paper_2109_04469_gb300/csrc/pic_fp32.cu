@@ -41,11 +41,12 @@ namespace pic {
 #endif
 
 constexpr int kWarps32 = kBlock / 32;
-constexpr int kRoundPerWarp = 4064;  // particles a warp handles between counter flushes
-// A counter takes at most two full weights per particle of the round (the particle and one
-// birth: an ionization electron, or an electron emitted at a wall node by an ion), so
-// 8 warps x 4064 particles x 2 x 2^16 < 2^32: the 32-bit counters of a block cannot overflow
-// between flushes.  4064 is a multiple of 32, so every round starts on a tile boundary.
+constexpr int kRoundPerWarp = 8160;  // particles a warp handles between counter flushes
+// A block's 32-bit counters of species s take one full weight (2^16) at most per particle of
+// species s (births add their charge straight to the 64-bit counts), so 8 warps x 8160
+// particles x 2^16 < 2^32: they cannot overflow between flushes, and the electron counters
+// are left alone by the ion pass (and the ion counters by the electron pass).  8160 is a
+// multiple of 32, so every round starts on a tile boundary.
 constexpr unsigned short kCdFlag = 0x8000;  // countdown expires without a candidate
 constexpr int kPurCount = 4;                 // stream purpose: countdown of a new particle
 
@@ -134,6 +135,17 @@ __device__ __forceinline__ void deposit32(unsigned* C, int j, float f) {
   atomicAdd(&C[j + 1], (unsigned)wr);
 }
 
+// A newborn particle of species s (rare): the same weights, added straight to the next
+// step's 64-bit counts (the block's counters hold the units of 2^-16 that a flush shifts by
+// 16 bits), so that those counters take one weight per particle of their own species only.
+__device__ __forceinline__ void deposit_birth(const DevCtx* G, unsigned step, int s, int j,
+                                              float f) {
+  unsigned long long* Cn = G->C + (size_t)(((step + 1) & 1) * 2 + s) * G->nx;
+  const int wr = __float2int_rn(f * 65536.0f);
+  if (wr != 65536) atomicAdd(&Cn[j], (unsigned long long)(65536 - wr) << 16);
+  if (wr != 0) atomicAdd(&Cn[j + 1], (unsigned long long)wr << 16);
+}
+
 // (cell, off) with off brought back into [0, 1)
 __device__ __forceinline__ void renorm(int& c, float& off) {
   const float k = floorf(off);
@@ -161,7 +173,7 @@ struct SurfOut {  // state after step 5; flags: bit 0 removed, bit 1 electron em
 template <int S>
 __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned step, long long p,
                                           int cell, float off, float vx, bool left,
-                                          unsigned* sCe, Rec32* em) {
+                                          Rec32* em) {
   const int nc = G->nc;
   unsigned ev = 0u;
   const unsigned pid = G->id[S][p];
@@ -207,7 +219,7 @@ __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned
     r.cd = draw_countdown(next_u(se), G->f_lnq[0]);
     *em = r;
     flags |= 2;
-    deposit32(sCe, r.cell, r.off);
+    deposit_birth(G, step, 0, r.cell, r.off);
     ev |= 1u << kCnSee;
   }
   return SurfOut{cell, off, vx, flags, ev};
@@ -226,7 +238,7 @@ struct CollOut {  // state after step 6; born: an ionization pair was written
 template <int S>
 __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned step, long long p,
                                           int cell, float off, float vx, unsigned cd,
-                                          unsigned* sCe, unsigned* sCi, Rec32* re, Rec32* ri) {
+                                          Rec32* re, Rec32* ri) {
   const unsigned pid = G->id[S][p];  // one round trip with vy, vz
   float vy = G->fvy[S][p], vz = G->fvz[S][p];  // in flight during the draws below
   Stream sc(*G, S, kPurColl, pid, step);
@@ -277,8 +289,8 @@ __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned
         *ri = Rec32{cell, off, g0 * G->f_sig_i, g1 * G->f_sig_i, g2 * G->f_sig_i,
                     draw_countdown(next_u(sc), G->f_lnq[1])};
         born = 1;
-        deposit32(sCe, cell, off);
-        deposit32(sCi, cell, off);
+        deposit_birth(G, step, 0, cell, off);
+        deposit_birth(G, step, 1, cell, off);
         ev |= 1u << kCnEIon;
       }
     }
@@ -413,7 +425,7 @@ __device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step
     if (c.pk >> 31) {  // step 5: left the gap
       cell = (int)(short)(c.aux & 0xFFFFu);
       const bool left = cell < 0 || (cell == 0 && off == 0.0f);
-      const SurfOut r = surface32<S>(G, step, p, cell, off, vx, left, sCe, &P.recE[lane]);
+      const SurfOut r = surface32<S>(G, step, p, cell, off, vx, left, &P.recE[lane]);
       ev |= r.ev;
       cell = r.cell;
       off = r.off;
@@ -430,7 +442,7 @@ __device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step
     if (!dead) {
       if ((cd & 0x7FFFu) == 0u) {  // the countdown ran out: step 6
         const CollOut o =
-            collide32<S>(G, step, p, cell, off, vx, cd, sCe, sCi, &P.recE[lane], &P.recI[lane]);
+            collide32<S>(G, step, p, cell, off, vx, cd, &P.recE[lane], &P.recI[lane]);
         ev |= o.ev;
         vx = o.vx;
         cd = o.cd;
@@ -874,9 +886,8 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
   __shared__ int wc[5][kWarps32];
   __shared__ long long wb[2][kWarps32];
   block_pass32<0>(K, step, ne, sE, sC, sCnt, Cn, P, Q, wc, wb);
-  // when every warp's electron and ion ranges together fit one round, the counters stay in
-  // range across both passes and each warp goes on to its ions without waiting for the block
-  if (warp_range_max(ne) + warp_range_max(ni) > kRoundPerWarp) flush32(K, sC, Cn);
+  // no flush between the species: the ion pass adds nothing to the electron counters, so
+  // each warp goes on to its ions without waiting for the block
   block_pass32<1>(K, step, ni, sE + nx, sC, sCnt, Cn, P, Q, wc, wb);
   flush32(K, sC, Cn);  // ends with a block barrier: every warp's lists are complete
   if (threadIdx.x < kNumCounters && sCnt[threadIdx.x])
