@@ -1178,7 +1178,6 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
   __shared__ long long sNe[kMaxEnsemble], sNi[kMaxEnsemble], sIt[kMaxEnsemble + 1];
   __shared__ unsigned sStep[kMaxEnsemble];
   __shared__ int sG[kMaxEnsemble], sC0[kMaxEnsemble + 1], sOrd[kMaxEnsemble];
-  __shared__ int sUpw[kMaxEnsemble];  // owners per warp per chunk
   __shared__ Divider sGd[kMaxEnsemble];  // dividers of the owner counts
   __shared__ unsigned sChunk;
   __shared__ unsigned long long sCnt[kNumCounters];
@@ -1202,12 +1201,6 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
     sStep[s] = step;
     sG[s] = active ? (int)g : 0;
     sGd[s] = make_divider(g);
-    // owners per warp between counter flushes: an owner's range of species s holds fewer
-    // than ceil(n_s / G) + 64 particles (32-particle rounding); keep the warp's sum within
-    // kEnsSpeciesRound so the 32-bit shared counters stay in range (per <= kEnsSpeciesRound
-    // by the owner count above, and the capacity check at creation)
-    const long long per = (nmax + g - 1) / g + 64;
-    sUpw[s] = (int)max(1ll, (long long)kEnsSpeciesRound / per);
     if (active && blockIdx.x == 0) snapshot_pass(*E->sims[s], step, ne, ni);
   }
   if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
@@ -1219,8 +1212,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
       const int s = E->order[k];
       sOrd[k] = s;
       sC0[k] = run;
-      const int span = kWarps32 * sUpw[s];
-      run += (sG[s] + span - 1) / span;
+      run += (sG[s] + kWarps32 - 1) / kWarps32;
     }
     sC0[n] = run;
   }
@@ -1279,9 +1271,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
       const long long ne = sNe[s], ni = sNi[s];
       const int G = sG[s], gs = E->gstride[s];
       unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
-      const int upw = sUpw[s];
-      for (int u = 0; u < upw; ++u) {
-      const long long g = (long long)(c - (unsigned)sC0[k]) * kWarps32 * upw + u * kWarps32 + warp;
+      const long long g = (long long)(c - (unsigned)sC0[k]) * kWarps32 + warp;
       if (g < G) {
         // after a timed-out wait (status set) the warp's remaining owners list nothing
         const Divider& dG = sGd[s];
@@ -1308,8 +1298,10 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
           if (bi) atomicAdd(&t[4], bi);
         }
       }
-      }
-      flush32(K, sC, Cn);  // upw owners per warp per chunk: the counters stay in range
+      // one owner per warp per chunk: an owner's range of species s holds fewer than
+      // ceil(n_s / G) + 64 <= kEnsSpeciesRound particles (32-particle rounding; the owner
+      // count above and the capacity check at creation), so the 32-bit counts stay in range
+      flush32(K, sC, Cn);
     }
     if (cur >= 0 && threadIdx.x < kNumCounters && sCnt[threadIdx.x])
       atomicAdd(&E->sims[sOrd[cur]]->counters[threadIdx.x], sCnt[threadIdx.x]);
