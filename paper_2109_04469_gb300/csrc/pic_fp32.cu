@@ -135,11 +135,11 @@ __device__ __forceinline__ void deposit32(unsigned* C, int j, float f) {
   atomicAdd(&C[j + 1], (unsigned)wr);
 }
 
-// A newborn particle of species s (rare): the same weights, added straight to the next
-// step's 64-bit counts (the block's counters hold the units of 2^-16 that a flush shifts by
-// 16 bits), so that those counters take one weight per particle of their own species only.
-__device__ __forceinline__ void deposit_birth(const DevCtx* G, unsigned step, int s, int j,
-                                              float f) {
+// A newborn particle of species s (rare) whose charge does not go into the block's counters:
+// the same weights, straight into the next step's 64-bit counts (the block's counters hold
+// the units of 2^-16 that a flush shifts by 16 bits).
+__device__ __forceinline__ void deposit_birth64(const DevCtx* G, unsigned step, int s, int j,
+                                                float f) {
   unsigned long long* Cn = G->C + (size_t)(((step + 1) & 1) * 2 + s) * G->nx;
   const int wr = __float2int_rn(f * 65536.0f);
   if (wr != 65536) atomicAdd(&Cn[j], (unsigned long long)(65536 - wr) << 16);
@@ -219,7 +219,6 @@ __device__ __noinline__ SurfOut surface32(const DevCtx* __restrict__ G, unsigned
     r.cd = draw_countdown(next_u(se), G->f_lnq[0]);
     *em = r;
     flags |= 2;
-    deposit_birth(G, step, 0, r.cell, r.off);
     ev |= 1u << kCnSee;
   }
   return SurfOut{cell, off, vx, flags, ev};
@@ -289,8 +288,6 @@ __device__ __noinline__ CollOut collide32(const DevCtx* __restrict__ G, unsigned
         *ri = Rec32{cell, off, g0 * G->f_sig_i, g1 * G->f_sig_i, g2 * G->f_sig_i,
                     draw_countdown(next_u(sc), G->f_lnq[1])};
         born = 1;
-        deposit_birth(G, step, 0, cell, off);
-        deposit_birth(G, step, 1, cell, off);
         ev |= 1u << kCnEIon;
       }
     }
@@ -376,6 +373,11 @@ constexpr int kCandQ = 160;  // up to 31 waiting + 128 from one tile
 struct __align__(16) WarpRare {
   Rec32 recE[32], recI[32];  // the lanes' births of the current drain
   Cand cq[kCandQ];
+  // births' charge goes into the block's counters while the warp's budget lasts (nb birth
+  // deposits there since its last flush, at most bud), else into the 64-bit counts; the
+  // budget keeps the counters' bound (bud = 0 in the single run, whose counter rounds fill
+  // the bound with particles of the counter's own species)
+  int nb, bud;
 };
 template <int NS>
 struct __align__(128) WarpPipe {  // one per warp, back to back in shared memory
@@ -472,6 +474,25 @@ __device__ __noinline__ int2 drain32(const DevCtx* __restrict__ G, unsigned step
   }
   const unsigned mh = __ballot_sync(0xffffffffu, dead);
   const unsigned mb = __ballot_sync(0xffffffffu, born);
+  if (mb) {  // the births' charge: an ionization pair at the electron, an emitted electron
+    const int nd = __popc(mb) * (S == 0 ? 2 : 1);  // deposits
+    int nb = 0;
+    if (lane == 0) nb = P.nb;
+    nb = __shfl_sync(0xffffffffu, nb, 0);
+    const bool blk = nb + nd <= P.bud;  // warp-uniform
+    if (born) {
+      const Rec32& re = P.recE[lane];
+      if (blk) {
+        deposit32(sCe, re.cell, re.off);
+        if (S == 0) deposit32(sCi, re.cell, re.off);  // the ion is born at the electron
+      } else {
+        deposit_birth64(G, step, 0, re.cell, re.off);
+        if (S == 0) deposit_birth64(G, step, 1, re.cell, re.off);
+      }
+    }
+    __syncwarp();
+    if (blk && lane == 0) P.nb = nb + nd;
+  }
   if (dead) G->hole_idx[S][hk + __popc(mh & lt)] = (int)p;
   if (born) {
     const size_t cap = (size_t)G->nchunk_max * kChunk;
@@ -867,6 +888,8 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_push_fp32(DevCt
   if ((threadIdx.x & 31) == 0) {
     for (int s = 0; s < kStagesRun; ++s) mbar_init(&P.bar[s], 1u);
     fence_mbar_init();
+    P.r.nb = 0;
+    P.r.bud = 0;  // births to the 64-bit counts
   }
   PipeCount Q{0u, 0u};
   for (int j = threadIdx.x; j < 2 * nx; j += blockDim.x) sC[j] = 0u;
@@ -1179,6 +1202,7 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
   __shared__ unsigned sStep[kMaxEnsemble];
   __shared__ int sG[kMaxEnsemble], sC0[kMaxEnsemble + 1], sOrd[kMaxEnsemble];
   __shared__ Divider sGd[kMaxEnsemble];  // dividers of the owner counts
+  __shared__ int sBud[kMaxEnsemble];     // births an owner may deposit into the block's counts
   __shared__ unsigned sChunk;
   __shared__ unsigned long long sCnt[kNumCounters];
   __shared__ CompactTot sT[2];
@@ -1201,6 +1225,10 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
     sStep[s] = step;
     sG[s] = active ? (int)g : 0;
     sGd[s] = make_divider(g);
+    // a count of species s takes per chunk at most 2^16 per particle of that species (fewer
+    // than ceil(n_s / G) + 64 of them per owner, 32-particle rounding) and per birth in the
+    // block's counts: 8 owners x (per + budget) <= 8 x 8191 keeps it below 2^32
+    sBud[s] = 8191 - (int)((nmax + g - 1) / g + 64);
     if (active && blockIdx.x == 0) snapshot_pass(*E->sims[s], step, ne, ni);
   }
   if (threadIdx.x < kNumCounters) sCnt[threadIdx.x] = 0ull;
@@ -1273,6 +1301,11 @@ __global__ void __launch_bounds__(kBlock, PIC_FP32_MIN_BLOCKS) k_ensemble_step(E
       unsigned long long* Cn = K.C + (size_t)(((step + 1) & 1) * 2) * nx;
       const long long g = (long long)(c - (unsigned)sC0[k]) * kWarps32 + warp;
       if (g < G) {
+        if (lane == 0) {
+          P.r.nb = 0;
+          P.r.bud = sBud[s];
+        }
+        __syncwarp();
         // after a timed-out wait (status set) the warp's remaining owners list nothing
         const Divider& dG = sGd[s];
         const long long q0 = range_begin_d(ne, (int)g, dG), q1 = range_begin_d(ne, (int)g + 1, dG);
