@@ -325,11 +325,16 @@ __host__ __device__ __forceinline__ int prefix_stride(int G) { return (G + 3) & 
 // The single run's placement launch also keeps the list bases of its nlist owners in shared
 // memory, after the five prefix arrays: sb[s * prefix_stride(G + 1) + b] = list_base(N_s, b,
 // G) for b = 0..G, formed once per block (multiply-high by K.nl_div) instead of by 64-bit
-// divisions in every item.
+// divisions in every item.  After them, per species, the hole list of the owner of the new
+// count N_n when it holds at most kStagedHoles entries (the block reads it anyway to count
+// the holes below N_n, and most tail positions lie in that owner): st[s] = that owner, or -1,
+// and its entries at st + 4 + s * kStagedHoles.
+constexpr int kStagedHoles = 256;
 __host__ __device__ __forceinline__ size_t place_run_smem_bytes(int nx, int nlist) {
   const size_t field = sizeof(__int128) * (size_t)nx;
   const size_t lists = sizeof(int) * (5 * (size_t)prefix_stride(nlist) +
-                                      2 * (size_t)prefix_stride(nlist + 1));
+                                      2 * (size_t)prefix_stride(nlist + 1) + 4 +
+                                      2 * (size_t)kStagedHoles);
   return field > lists ? field : lists;
 }
 
@@ -477,13 +482,21 @@ __device__ void list_prefixes(const DevCtx& K, int G, int gstride, int* sp, Comp
     Beff2[s] = B2[s] < limit ? B2[s] : limit;
     Nn2[s] = N2[s] - H2[s] + Beff2[s];
     owner[s] = -1;
+    if (kSB && threadIdx.x == 0) sb[2 * Gb + s] = -1;  // no staged list (yet)
     if (H2[s] > Beff2[s]) {
       const int b = kSB ? upper_bound_i(sb + s * Gb, G, Nn2[s]) - 1 : range_owner(N2[s], Nn2[s], G);
       owner[s] = b;
       const int* list = K.hole_idx[s] + (kSB ? (long long)sb[s * Gb + b] : list_base(N2[s], b, G));
       const int m = (b + 1 < G ? sp[s * Gp + b + 1] : H2[s]) - sp[s * Gp + b];
+      int* st = sb + 2 * Gb;  // (kSB) the staged list of this owner
+      const bool stage = kSB && m <= kStagedHoles;
+      if (kSB && threadIdx.x == 0) st[s] = stage ? b : -1;
       unsigned below = 0;
-      for (int r = threadIdx.x; r < m; r += NT) below += ((long long)list[r] < Nn2[s]) ? 1u : 0u;
+      for (int r = threadIdx.x; r < m; r += NT) {
+        const int h = list[r];
+        below += ((long long)h < Nn2[s]) ? 1u : 0u;
+        if (stage) st[4 + s * kStagedHoles + r] = h;
+      }
       below = __reduce_add_sync(0xffffffffu, below);
       if (lane == 0 && below) atomicAdd(&sq[s], (int)below);
     }
@@ -597,6 +610,7 @@ __device__ __forceinline__ void place_items(const DevCtx& K, int G, const int* s
       const typename P::Rec rec = P::load(K, s, idx);
       const int b = kSB ? upper_bound_i(sbs, G, idx) - 1 : range_owner(t.N, idx, G);
       const int* list = K.hole_idx[s] + (kSB ? (long long)sbs[b] : list_base(t.N, b, G));
+      if (kSB && sb[2 * Gb + s] == b) list = sb + 2 * Gb + 4 + s * kStagedHoles;  // staged
       const int m = (b + 1 < G ? hp[b + 1] : (int)t.H) - hp[b];
       bool is_hole;
       const int lb = find_sorted(list, m, idx, is_hole);
